@@ -1,0 +1,134 @@
+/*
+ * psq.h - C ABI of the GB300 prolate-spheroidal (PS) quadrature library for Slater-type
+ * orbital (STO) integrals.
+ *
+ * Method: Stark et al., "Numerical Integration of Slater Basis Functions Over Prolate
+ * Spheroidal Grids" (arXiv 2510.15204).  For every atom pair a PS grid (Section 2.1,
+ * eqs 2-7, 10-12, 17; Algorithms 1-2) is built, refined around a third centre where a
+ * 3-centre term needs it (Section 2.2, Fig. 2, parameter N_SP).  STOs (eq 1) and the
+ * Coulomb potentials of RI auxiliary functions (eqs 15-16) are evaluated on its points and
+ * contracted by eq 9 into overlap S, kinetic T, nuclear attraction V, 2-centre (P|Q) and
+ * 3-centre (P|ij) matrices.  Polyatomics are assembled from grids over at most three atoms
+ * (Section 4): every matrix element is integrated on exactly one grid, picked by the
+ * distinct centres of its integrand (one centre: the pair grid of that atom and its nearest
+ * neighbour, ties to the lower index; two: their pair grid; three: the pair grid of the two
+ * basis-function atoms refined around the third).
+ *
+ * Conventions.  Atomic units (bohr).  Shells must be listed grouped by atom in ascending
+ * atom order.  Function order: atom, then shell as listed, then m = -l..l of real
+ * orthonormal spherical harmonics (no Condon-Shortley phase).  Radial normalisation
+ * N = (2 zeta)^(n+1/2) / sqrt((2n)!).  Pair (A,B) puts the lower atom index A at (0,0,+a).
+ * Kinetic integrals use -1/2 chi_a lap chi_b symmetrised, (P|Q) is symmetrised.
+ *
+ * Errors.  Every call returns a psq_status; no call throws or aborts.  psq_last_error()
+ * gives a message for the calling thread's last failure.  On a failed call no output has
+ * been written unless the status is PSQ_ERR_CUDA / PSQ_ERR_TIMEOUT raised by a kernel, in
+ * which case outputs are undefined.
+ *
+ * Memory.  The library allocates no device memory of its own for a computation: the
+ * caller passes a device workspace (size from psq_job_workspace) and device output
+ * buffers.  Jobs copy their inputs at creation; the caller may free them afterwards.  A
+ * job holds a small page-locked host staging buffer for its tables.
+ */
+#ifndef PSQ_H
+#define PSQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PSQ_OK = 0,
+  PSQ_ERR_ARG = 1,         /* invalid argument: bad Z, l >= n, zeta <= 0, sizes, pointers */
+  PSQ_ERR_OOM = 2,         /* host allocation failed or workspace too small */
+  PSQ_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  PSQ_ERR_TIMEOUT = 4,     /* a bounded device wait expired; the context stays usable */
+  PSQ_ERR_GEOMETRY = 5,    /* coincident atoms or an unusable pair geometry */
+  PSQ_ERR_UNSUPPORTED = 6  /* e.g. a single atom, l > 6, Q > 16 */
+} psq_status;
+
+typedef struct { int Z; double xyz[3]; } psq_atom;             /* Z >= 0, position in bohr */
+typedef struct { int atom, n, l; double zeta; } psq_shell;      /* n > l >= 0, zeta > 0     */
+
+/* The five grid variables of Section 3 (N_mu, N_nu, N_phi, Q, N_SP), with Q per dimension
+ * as Algorithm 2 allows: n_mu x n_nu x n_phi volume elements, q_mu x q_nu x q_phi
+ * Gauss-Legendre points in each, and each volume element touching a third centre split
+ * n_sp times per dimension.  1 <= q <= 16; a refined grid needs n_mu, n_nu >= 2. */
+typedef struct { int n_mu, n_nu, n_phi, q_mu, q_nu, q_phi, n_sp; } psq_grid_spec;
+
+typedef enum {
+  PSQ_FP64 = 0,  /* plain path: every step in FP64 */
+  PSQ_MIXED = 1  /* FP64 grid, weights, potentials and accumulation; FP32 STO values;
+                    contraction on tcgen05 tensor cores with 3-piece BF16 splits */
+} psq_precision;
+
+enum { PSQ_S = 1, PSQ_T = 2, PSQ_V = 4, PSQ_J2 = 8, PSQ_J3 = 16, PSQ_ALL = 31 };
+
+typedef struct psq_context psq_context;
+typedef struct psq_job psq_job;
+
+/* Binds a context to a CUDA device (makes it current on the calling thread). */
+psq_status psq_context_create(int device, psq_context** out);
+psq_status psq_context_destroy(psq_context* ctx);
+
+/* Plans a job: validates and copies atoms and shells, builds every pair frame, the cell
+ * edges (eq 7, 12, 17), the third-centre line moves and splits (Section 2.2) and the
+ * block assignment.  pair_specs holds n_atoms*(n_atoms-1)/2 specs in pair order
+ * (0,1),(0,2)..(0,n-1),(1,2).. or a single spec for every pair (n_specs == 1). */
+psq_status psq_job_create(psq_context* ctx, const psq_atom* atoms, int n_atoms,
+                          const psq_shell* basis, int n_basis_shells,
+                          const psq_shell* aux, int n_aux_shells,
+                          const psq_grid_spec* pair_specs, int n_specs,
+                          psq_precision precision, psq_job** out);
+psq_status psq_job_destroy(psq_job* job);
+
+/* Basis and aux function counts. */
+psq_status psq_job_sizes(const psq_job* job, int* n_bf, int* n_aux);
+
+/* Device workspace bytes psq_compute needs for the classes in mask. */
+psq_status psq_job_workspace(const psq_job* job, unsigned mask, size_t* bytes);
+
+/* Job statistics: number of grids, total quadrature points (over the grids mask needs),
+ * useful contractions (sum over integrated blocks of rows x cols x points, each (P,i<=j)
+ * once on a same-atom pair), and kernel launches psq_compute issues for mask. */
+psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_t* n_points,
+                         double* contractions, int* launches);
+
+/* Computes the classes in mask, asynchronously on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  d_out[0..4] are device buffers for S, T, V (n_bf*n_bf doubles each,
+ * row-major), J2 (n_aux*n_aux) and J3 (n_aux*n_bf*n_bf, [P][i][j]); entries for classes
+ * not in mask may be NULL.  d_workspace: at least psq_job_workspace(mask) bytes of device
+ * memory, 256-byte aligned.  The caller synchronises the stream before reading outputs. */
+psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes,
+                       double* d_out[5], void* stream);
+
+/* psq_compute followed by device-to-host copies of the requested classes into h_out[0..4]
+ * (page-locked memory recommended) and a synchronisation of the stream. */
+psq_status psq_compute_host(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes,
+                            double* d_out[5], double* h_out[5], void* stream);
+
+/* Diagnostics for step-by-step parity tests. */
+/* Grid g (0 <= g < n_grids): its atoms (C = -1 for an unrefined pair grid), point count. */
+psq_status psq_job_grid_info(const psq_job* job, int g, int* A, int* B, int* C, int64_t* n_points);
+/* Writes the points of grid g into d_out (8 rows of n_points doubles: x, y, z in the
+ * molecule frame, w, r_A, r_B, and the flat index of the point's volume element... rows 6-7
+ * are mu and nu).  Points of volume elements that are split around a third centre carry
+ * w = 0 at their unsplit positions; the split sub-cells follow the regular ones. */
+psq_status psq_job_grid_points(psq_job* job, int g, double* d_out, void* stream);
+/* Evaluates on grid g: kind 0 = basis chi of the grid's two pair atoms (rows in function
+ * order), 1 = their kinetic operand lap chi, 2 = aux chi, 3 = aux potentials V^P (aux of
+ * both pair atoms for an unrefined grid, of the third centre for a refined one).  d_out
+ * holds rows x n_points doubles; *rows receives the row count. */
+psq_status psq_job_grid_functions(psq_job* job, int g, int kind, void* d_workspace,
+                                  size_t ws_bytes, double* d_out, int* rows, void* stream);
+
+/* Thread-local message describing the calling thread's last error. */
+const char* psq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSQ_H */
