@@ -1,0 +1,292 @@
+#!/usr/bin/env python
+"""Throughput of the PS-quadrature hot path on one GB300 (or N independent replicas).
+
+One step = one psq_compute of a whole job (grid + weights, STO and aux-potential evaluation,
+contraction, reduction, assembly of every requested integral class) on synthetic inputs
+resident in device memory.  Metric: useful point-basis^2 contractions per second (one
+contraction = one w f g multiply-accumulate into one matrix element; the count follows the
+assembly rule: every matrix element integrated once on one grid).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload triatomic_oh2]
+                    [--precision fp64|mixed] [--impl psq|reference]
+
+Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle (the paper's
+method written plainly in numpy FP64) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pt·basis² contractions/s vs plain FP64; serve p50/p99 latency at err≤1e-9"
+UNIT = "contractions/s"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is provided)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="psq", choices=["psq", "reference"])
+    ap.add_argument("--workload", default="triatomic_oh2")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(job):
+    """A bounded sample of the workload for the CPU oracle: the sub-molecule of atoms 0 and 1
+    (their basis and aux shells, the same grid spec and classes), i.e. one pair grid."""
+    import synth
+    keep = (0, 1)
+    basis = [s for s in job.basis if s[0] in keep]
+    aux = [s for s in job.aux if s[0] in keep]
+    spec = job.spec_for_pair(0, 1)
+    sub = synth.Job(job.name + "_pair01", job.atoms[:2], basis, aux, [spec], job.mask)
+    return sub, "atoms 0-1 of %s (one %dx%dx%d Q%d%d%d pair grid, %s classes)" % (
+        job.name, spec[0], spec[1], spec[2], spec[3], spec[4], spec[5], "all" if job.mask == 31 else job.mask)
+
+
+def time_oracle(job, min_seconds=10.0, max_runs=20):
+    import oracle
+    sub, desc = oracle_sample(job)
+    work = oracle.contractions(sub, sub.mask)
+    runs, t0 = 0, time.perf_counter()
+    while True:
+        oracle.compute(sub, mask=sub.mask, with_abs=False)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or runs >= max_runs:
+            break
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": work * runs / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%s, %d run(s), %.1f s, numpy FP64 (BLAS threads = all cores)" % (desc, runs, el)}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    job = synth.WORKLOADS[args.workload](args.seed)
+    sub, desc = oracle_sample(job)
+    work = oracle.contractions(sub, sub.mask)
+    for _ in range(args.warmup):
+        oracle.compute(sub, mask=sub.mask, with_abs=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.compute(sub, mask=sub.mask, with_abs=False)
+    el = time.perf_counter() - t0
+    value = work * args.steps / el
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "seed": args.seed, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ traffic record
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json, if recorded for the
+    current kernel source (null once the source changed since the counters were taken)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))[kernel][workload]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2510_15204_gb300", "csrc", rec["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["bytes_per_launch"] if h == rec["sha"] else None
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    rank, world, local = dist_env()
+    import torch
+    import synth
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_2510_15204_gb300 import build as B
+    B.build()
+    import paper_2510_15204_gb300 as P
+
+    job = synth.WORKLOADS[args.workload](args.seed)
+    mask = job.mask
+    ctx = P.Context(local)
+    prec = P.MIXED if args.precision == "mixed" else P.FP64
+    J = P.Job.from_synth(ctx, job, prec)
+    st = J.stats(mask)
+    ws, out = J.alloc(mask)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            J.compute(mask, ws, out, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    J.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J.compute(mask, ws, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    J.profile(False)
+    prof = J.profile_read()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * st["contractions"] * args.steps / (ms / 1e3)
+
+    # end to end through the C ABI with host buffers (tables up, matrices down, every step)
+    host = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in out.items()}
+    with torch.cuda.stream(stream):
+        J.compute_host(mask, ws, out, host, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            J.compute_host(mask, ws, out, host, stream)
+        e2e_s = time.perf_counter() - t0
+    h2d, d2h = J.io_bytes(mask)
+    e2e_val = st["contractions"] * args.e2e_steps / e2e_s
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * st["contractions"] * args.e2e_steps / float(t.item())
+
+    # roofline of the dominant kernel, timed live inside the timed region
+    kind = max(prof, key=lambda k: prof[k][0])
+    kms, kcount = prof[kind]
+    per_launch_s = kms / kcount / 1e3
+    if kind == "contract":
+        flops = 2.0 * st["contractions"]
+        if prec == P.FP64:
+            roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+        else:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+            roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": peaks["bf16_tflops"],
+                    "unit": "TFLOP/s", "peak_source": "measured bf16 burst"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    roof["kernel"] = kind
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
+    roof["traffic"] = recorded_traffic(kind, args.workload)
+    roof["share"] = kms / sum(v[0] for v in prof.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == P.FP64 else "f32+bf16x3",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "seed": args.seed, "precision": args.precision,
+                   "n_bf": J.n_bf, "n_aux": J.n_aux, "grids": st["grids"], "points": st["points"],
+                   "contractions_per_step": st["contractions"], "classes": "S,T,V,J2,J3" if mask == 31 else mask,
+                   "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" % (J.workspace_bytes(mask) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": st["launches"] * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle(job)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -70,7 +70,8 @@ enum { PSQ_S = 1, PSQ_T = 2, PSQ_V = 4, PSQ_J2 = 8, PSQ_J3 = 16, PSQ_ALL = 31 };
 typedef struct psq_context psq_context;
 typedef struct psq_job psq_job;
 
-/* Binds a context to a CUDA device (makes it current on the calling thread). */
+/* Binds a context to a CUDA device (makes it current on the calling thread).  device = -1
+ * makes a planning-only context: its jobs can be created, sized and queried, not computed. */
 psq_status psq_context_create(int device, psq_context** out);
 psq_status psq_context_destroy(psq_context* ctx);
 
@@ -110,14 +111,28 @@ psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws
 psq_status psq_compute_host(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes,
                             double* d_out[5], double* h_out[5], void* stream);
 
+/* Bytes psq_compute copies host-to-device (the job's tables) and psq_compute_host copies
+ * device-to-host (the requested matrices) per call. */
+psq_status psq_job_io_bytes(const psq_job* job, unsigned mask, size_t* h2d, size_t* d2h);
+
+/* Launch timing.  While enabled, psq_compute records a CUDA event on its stream before each
+ * step: 0 table upload, 1 grid + function evaluation, 2 contraction, 3 chunk reduction,
+ * 4 assembly (all classes).  psq_profile_read waits for the recorded events, returns the
+ * summed milliseconds and counts per step kind (8 slots) and clears the record. */
+psq_status psq_profile_enable(psq_job* job, int on);
+psq_status psq_profile_read(psq_job* job, double ms[8], int counts[8]);
+
 /* Diagnostics for step-by-step parity tests. */
-/* Grid g (0 <= g < n_grids): its atoms (C = -1 for an unrefined pair grid), point count. */
+/* Grid g of the PSQ_ALL plan (0 <= g < n_grids; pair grids (A<B) first, then the refined
+ * grids (A<B; C)): its atoms (C = -1 for an unrefined pair grid) and point count. */
 psq_status psq_job_grid_info(const psq_job* job, int g, int* A, int* B, int* C, int64_t* n_points);
-/* Writes the points of grid g into d_out (8 rows of n_points doubles: x, y, z in the
- * molecule frame, w, r_A, r_B, and the flat index of the point's volume element... rows 6-7
- * are mu and nu).  Points of volume elements that are split around a third centre carry
- * w = 0 at their unsplit positions; the split sub-cells follow the regular ones. */
-psq_status psq_job_grid_points(psq_job* job, int g, double* d_out, void* stream);
+/* Writes the points of grid g (Section 2.1 eqs 2-6, 10-11; Algorithm 2) into d_out: 8 rows
+ * of n_points doubles, x, y, z in the molecule frame, w, r_A, r_B, mu, nu.  Volume elements
+ * split around a third centre keep their unsplit points with w = 0; the split sub-cells
+ * follow the regular cells.  Uses the first psq_job_workspace(PSQ_ALL) bytes of d_workspace
+ * for tables. */
+psq_status psq_job_grid_points(psq_job* job, int g, void* d_workspace, size_t ws_bytes,
+                               double* d_out, void* stream);
 /* Evaluates on grid g: kind 0 = basis chi of the grid's two pair atoms (rows in function
  * order), 1 = their kinetic operand lap chi, 2 = aux chi, 3 = aux potentials V^P (aux of
  * both pair atoms for an unrefined grid, of the third centre for a refined one).  d_out

@@ -1,0 +1,261 @@
+"""Python binding of libpsq (prolate-spheroidal quadrature of STO integrals on GB300).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels behind the
+C ABI of ``include/psq.h``.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if ``libpsq.so`` is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpsq.so")
+
+S, T, V, J2, J3 = 1, 2, 4, 8, 16
+ALL = 31
+CLASSES = ("S", "T", "V", "J2", "J3")
+FP64, MIXED = 0, 1
+
+STATUS = {0: "PSQ_OK", 1: "PSQ_ERR_ARG", 2: "PSQ_ERR_OOM", 3: "PSQ_ERR_CUDA", 4: "PSQ_ERR_TIMEOUT",
+          5: "PSQ_ERR_GEOMETRY", 6: "PSQ_ERR_UNSUPPORTED"}
+
+
+class PsqError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+class psq_atom(ctypes.Structure):
+    _fields_ = [("Z", ctypes.c_int), ("xyz", ctypes.c_double * 3)]
+
+
+class psq_shell(ctypes.Structure):
+    _fields_ = [("atom", ctypes.c_int), ("n", ctypes.c_int), ("l", ctypes.c_int), ("zeta", ctypes.c_double)]
+
+
+class psq_grid_spec(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("n_mu", "n_nu", "n_phi", "q_mu", "q_nu", "q_phi", "n_sp")]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_VP, _I, _U, _SZ, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_size_t, ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = [
+    ("psq_context_create", _I, [_I, ctypes.POINTER(_VP)]),
+    ("psq_context_destroy", _I, [_VP]),
+    ("psq_job_create", _I, [_VP, ctypes.POINTER(psq_atom), _I, ctypes.POINTER(psq_shell), _I,
+                            ctypes.POINTER(psq_shell), _I, ctypes.POINTER(psq_grid_spec), _I, _I,
+                            ctypes.POINTER(_VP)]),
+    ("psq_job_destroy", _I, [_VP]),
+    ("psq_job_sizes", _I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    ("psq_job_workspace", _I, [_VP, _U, ctypes.POINTER(_SZ)]),
+    ("psq_job_stats", _I, [_VP, _U, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    ("psq_compute", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP]),
+    ("psq_compute_host", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("psq_job_grid_info", _I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                               ctypes.POINTER(ctypes.c_int64)]),
+    ("psq_job_grid_points", _I, [_VP, _I, _VP, _SZ, _VP, _VP]),
+    ("psq_job_grid_functions", _I, [_VP, _I, _I, _VP, _SZ, _VP, ctypes.POINTER(_I), _VP]),
+    ("psq_job_io_bytes", _I, [_VP, _U, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
+    ("psq_profile_enable", _I, [_VP, _I]),
+    ("psq_profile_read", _I, [_VP, _PD, ctypes.POINTER(_I)]),
+    ("psq_last_error", ctypes.c_char_p, []),
+]
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpsq.so is not built: run paper_2510_15204_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise PsqError(status, lib().psq_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A CUDA device bound to the library."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().psq_context_create(device, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().psq_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Job:
+    """An integral job: atoms (Z, (x, y, z)) in bohr, shells (atom, n, l, zeta), one grid spec
+    or one per atom pair (n_mu, n_nu, n_phi, q_mu, q_nu, q_phi, n_sp)."""
+
+    def __init__(self, ctx: Context, atoms, basis, aux, specs, precision: int = FP64):
+        self.ctx = ctx
+        A = (psq_atom * len(atoms))()
+        for i, (Z, xyz) in enumerate(atoms):
+            A[i].Z = int(Z)
+            for c in range(3):
+                A[i].xyz[c] = float(xyz[c])
+        Bs = (psq_shell * max(1, len(basis)))()
+        for i, (a, n, l, z) in enumerate(basis):
+            Bs[i].atom, Bs[i].n, Bs[i].l, Bs[i].zeta = int(a), int(n), int(l), float(z)
+        As = (psq_shell * max(1, len(aux)))()
+        for i, (a, n, l, z) in enumerate(aux):
+            As[i].atom, As[i].n, As[i].l, As[i].zeta = int(a), int(n), int(l), float(z)
+        Sp = (psq_grid_spec * len(specs))()
+        for i, s in enumerate(specs):
+            for k, v in zip(("n_mu", "n_nu", "n_phi", "q_mu", "q_nu", "q_phi", "n_sp"), s):
+                setattr(Sp[i], k, int(v))
+        h = ctypes.c_void_p()
+        _check(lib().psq_job_create(ctx.handle, A, len(atoms), Bs, len(basis), As, len(aux), Sp, len(specs),
+                                    int(precision), ctypes.byref(h)))
+        self.handle = h
+        nb, na = ctypes.c_int(), ctypes.c_int()
+        _check(lib().psq_job_sizes(h, ctypes.byref(nb), ctypes.byref(na)))
+        self.n_bf, self.n_aux = nb.value, na.value
+
+    @classmethod
+    def from_synth(cls, ctx, job, precision=FP64):
+        return cls(ctx, job.atoms, job.basis, job.aux, job.specs, precision)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().psq_job_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, mask=ALL) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().psq_job_workspace(self.handle, mask, ctypes.byref(n)))
+        return n.value
+
+    def stats(self, mask=ALL) -> dict:
+        g, p, c, n = ctypes.c_int(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int()
+        _check(lib().psq_job_stats(self.handle, mask, ctypes.byref(g), ctypes.byref(p), ctypes.byref(c),
+                                   ctypes.byref(n)))
+        return {"grids": g.value, "points": p.value, "contractions": c.value, "launches": n.value}
+
+    def out_shapes(self, mask=ALL):
+        nb, na = self.n_bf, self.n_aux
+        shapes = {"S": (nb, nb), "T": (nb, nb), "V": (nb, nb), "J2": (na, na), "J3": (na, nb, nb)}
+        return {k: shapes[k] for i, k in enumerate(CLASSES) if (mask >> i) & 1}
+
+    def alloc(self, mask=ALL, device=None):
+        """Device workspace and output tensors for mask (torch allocations)."""
+        import torch
+        dev = torch.device("cuda", self.ctx.device if device is None else device)
+        ws = torch.empty(max(256, self.workspace_bytes(mask)), dtype=torch.uint8, device=dev)
+        out = {k: torch.empty(s, dtype=torch.float64, device=dev) for k, s in self.out_shapes(mask).items()}
+        return ws, out
+
+    def compute(self, mask=ALL, ws=None, out=None, stream=None):
+        """Launches the computation on stream (default: torch's current stream); returns the
+        dict of output tensors.  Asynchronous: synchronise before reading."""
+        if ws is None or out is None:
+            ws2, out2 = self.alloc(mask)
+            ws = ws if ws is not None else ws2
+            out = out if out is not None else out2
+        ptrs = (ctypes.c_void_p * 5)()
+        for i, k in enumerate(CLASSES):
+            ptrs[i] = out[k].data_ptr() if k in out else None
+        _check(lib().psq_compute(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), ws.numel(), ptrs,
+                                 _stream_ptr(stream)))
+        return out
+
+    def compute_host(self, mask, ws, out, host_out, stream=None):
+        """compute() plus device-to-host copies into host_out (pinned CPU tensors) and a sync."""
+        d = (ctypes.c_void_p * 5)()
+        h = (ctypes.c_void_p * 5)()
+        for i, k in enumerate(CLASSES):
+            d[i] = out[k].data_ptr() if k in out else None
+            h[i] = host_out[k].data_ptr() if k in host_out else None
+        _check(lib().psq_compute_host(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), ws.numel(), d, h,
+                                      _stream_ptr(stream)))
+        return host_out
+
+    def io_bytes(self, mask=ALL):
+        h, d = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().psq_job_io_bytes(self.handle, mask, ctypes.byref(h), ctypes.byref(d)))
+        return h.value, d.value
+
+    PROFILE_KINDS = ("upload", "eval", "contract", "reduce", "assemble", "k5", "k6", "k7")
+
+    def profile(self, on: bool):
+        _check(lib().psq_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self):
+        """{kind: (total_ms, count)} of the launches recorded since the last read."""
+        ms = (ctypes.c_double * 8)()
+        cnt = (ctypes.c_int * 8)()
+        _check(lib().psq_profile_read(self.handle, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.PROFILE_KINDS) if cnt[i]}
+
+    # ------------------------------------------------------------- diagnostics
+    def grid_info(self, g):
+        A, B, C, K = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(lib().psq_job_grid_info(self.handle, g, ctypes.byref(A), ctypes.byref(B), ctypes.byref(C),
+                                       ctypes.byref(K)))
+        return A.value, B.value, (None if C.value < 0 else C.value), K.value
+
+    def n_grids(self):
+        return self.stats(ALL)["grids"]
+
+    def grid_points(self, g, stream=None):
+        import torch
+        K = self.grid_info(g)[3]
+        dev = torch.device("cuda", self.ctx.device)
+        ws = torch.empty(max(256, self.workspace_bytes(ALL)), dtype=torch.uint8, device=dev)
+        out = torch.empty((8, K), dtype=torch.float64, device=dev)
+        _check(lib().psq_job_grid_points(self.handle, g, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def grid_functions(self, g, kind, stream=None):
+        import torch
+        K = self.grid_info(g)[3]
+        dev = torch.device("cuda", self.ctx.device)
+        ws = torch.empty(max(256, self.workspace_bytes(ALL)) + (1 << 20) + 64 * (K // 128 + 1),
+                         dtype=torch.uint8, device=dev)
+        nrows = self.n_bf + self.n_aux  # upper bound
+        out = torch.empty((nrows, K), dtype=torch.float64, device=dev)
+        rows = ctypes.c_int()
+        _check(lib().psq_job_grid_functions(self.handle, g, kind, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                            ctypes.c_void_p(out.data_ptr()), ctypes.byref(rows),
+                                            _stream_ptr(stream)))
+        return out[: rows.value]

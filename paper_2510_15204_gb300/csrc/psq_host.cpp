@@ -1,0 +1,1015 @@
+// Host side of the PS quadrature library: C ABI, input validation, the planner that turns a
+// job (atoms, shells, grid specs) into device tables, and the launch sequence.
+//
+// Planner steps (independent of any other implementation in this repository):
+//  * pair frames (Section 2.1: foci at (0,0,+-a), grid rotated and translated onto a pair);
+//  * cell edges: mu = C1 atanh(i/(N_mu+1)), C1 = 2.3 a^(1/4); nu = j pi/N_nu; phi = 2 pi k/N_phi
+//    (eqs 7, 12, 17; Section 2.3);
+//  * third centre (Section 2.2, Fig. 2): frame turned so the centre sits at phi = 0, the
+//    nearest interior mu and nu lines moved onto it, the cells that touch it split N_SP ways;
+//  * assembly over grids of at most three atoms (Section 4): every matrix element is taken
+//    from one grid chosen by the distinct centres of its integrand;
+//  * Gauss-Legendre nodes (Newton on the Legendre recurrence) and harmonic norms.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/psq.h"
+#include "psq_internal.h"
+
+using namespace psq;
+
+namespace {
+
+thread_local std::string g_err;
+
+psq_status fail(psq_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(PSQ_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                            \
+  } while (0)
+
+constexpr double kOnAxisTol = 1e-10;  // a third centre this close (x a) to the axis is on it
+constexpr int kPointsPerBlock = 128;
+constexpr int kSmCount = 152;
+
+// Gauss-Legendre rule by Newton's method on P_q (Bonnet recurrence); nodes ascending.
+void gauss_legendre(int q, double* x, double* w) {
+  for (int i = 0; i < q; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= q; ++k) {
+        const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (q == 1) p0 = 1.0;
+      dp = q * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= q; ++k) {
+      const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (q == 1) p0 = 1.0;
+    dp = q * (z * p1 - p0) / (z * z - 1.0);
+    x[q - 1 - i] = z;  // z runs from the largest node down
+    w[q - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+double factorial(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+struct Vec3 {
+  double x, y, z;
+};
+Vec3 sub(Vec3 a, Vec3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+Vec3 add(Vec3 a, Vec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+Vec3 scale(Vec3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+double dot(Vec3 a, Vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+double norm(Vec3 a) { return std::sqrt(dot(a, a)); }
+Vec3 cross(Vec3 a, Vec3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+
+}  // namespace
+
+struct psq_context {
+  int device;
+};
+
+namespace {
+
+// Everything psq_compute needs for one class mask.
+struct Plan {
+  unsigned mask = 0;
+  std::vector<DevGrid> grids;
+  std::vector<double> edges;
+  std::vector<PointBlock> pblocks;
+  std::vector<GemmBlock> gblocks;
+  std::vector<GemmItem> items;
+  std::vector<short2> pairs;
+  std::vector<int64_t> elem_begin;
+  // assembly sources
+  std::vector<SrcEntry> src[4];
+  std::vector<int> src_ptr[4];
+  std::vector<J3Src> j3;
+  // workspace layout (bytes)
+  size_t table_bytes = 0, ops_off = 0, part_off = 0, res_off = 0, ws_bytes = 0;
+  size_t o_grids, o_edges, o_bsh, o_ash, o_xyz, o_pb, o_gb, o_it, o_pairs, o_eb;
+  size_t o_fa, o_fl, o_aa, o_al, o_src[4], o_ptr[4], o_j3;
+  double* staging = nullptr;  // copy of the tables, page-locked when pinned
+  bool pinned = false;
+  int64_t n_points = 0;
+  double contractions = 0;
+  int launches = 0;
+  ~Plan() {
+    if (staging && pinned) cudaFreeHost(staging);
+    if (staging && !pinned) std::free(staging);
+  }
+};
+
+}  // namespace
+
+struct psq_job {
+  psq_context* ctx;
+  int nat;
+  std::vector<psq_atom> atoms;
+  std::vector<psq_shell> basis, aux;
+  std::vector<psq_grid_spec> specs;
+  psq_precision prec;
+  std::vector<int> nb, na, sb0, sb1, sa0, sa1, fn_atom, fn_local, aux_atom, aux_local, nn;
+  std::vector<DevShell> dbs, das;
+  int nbf = 0, naux = 0;
+  std::map<unsigned, std::unique_ptr<Plan>> plans;
+  std::mutex mu;
+  // launch timing: events recorded on the compute stream, read back on request
+  struct ProfRec { int kind; cudaEvent_t ev; };
+  bool prof_on = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_free;
+  ~psq_job() {
+    for (auto& r : prof) cudaEventDestroy(r.ev);
+    for (auto e : ev_free) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+Vec3 pos(const psq_job* j, int X) { return {j->atoms[X].xyz[0], j->atoms[X].xyz[1], j->atoms[X].xyz[2]}; }
+
+const psq_grid_spec& spec_for(const psq_job* j, int A, int B) {
+  if (j->specs.size() == 1) return j->specs[0];
+  if (A > B) std::swap(A, B);
+  const int n = j->nat;
+  return j->specs[A * n - A * (A + 1) / 2 + (B - A - 1)];
+}
+
+// Grid of the term with basis atoms A, B and operator / aux atom C, by its distinct centres.
+struct GridKey {
+  int A, B, C;  // C = -1: unrefined pair grid
+  bool operator<(const GridKey& o) const {
+    if (A != o.A) return A < o.A;
+    if (B != o.B) return B < o.B;
+    return C < o.C;
+  }
+};
+
+GridKey grid_for(const psq_job* j, int A, int B, int C) {
+  int s[3] = {A, B, C};
+  std::sort(s, s + 3);
+  const int nd = 1 + (s[1] != s[0]) + (s[2] != s[1]);
+  if (nd == 1) {
+    const int X = s[0], Y = j->nn[X];
+    return {std::min(X, Y), std::max(X, Y), -1};
+  }
+  if (nd == 2) return {s[0], s[2], -1};
+  return {std::min(A, B), std::max(A, B), C};
+}
+
+// Pair frame and third-centre placement of one grid.
+psq_status build_grid(const psq_job* j, GridKey key, DevGrid& g, std::vector<double>& edges) {
+  std::memset(&g, 0, sizeof(g));
+  const psq_grid_spec& sp = spec_for(j, key.A, key.B);
+  const Vec3 RA = pos(j, key.A), RB = pos(j, key.B);
+  const Vec3 d = sub(RA, RB);
+  const double R = norm(d);
+  const double a = 0.5 * R;
+  const Vec3 M = scale(add(RA, RB), 0.5);
+  const Vec3 ez = scale(d, 1.0 / R);
+  Vec3 ex{0, 0, 0};
+  bool have_ex = false;
+  Vec3 RC{0, 0, 0};
+  if (key.C >= 0) {
+    RC = pos(j, key.C);
+    const Vec3 v = sub(RC, M);
+    const Vec3 perp = sub(v, scale(ez, dot(v, ez)));
+    const double pn = norm(perp);
+    if (pn > kOnAxisTol * a) {
+      ex = scale(perp, 1.0 / pn);
+      have_ex = true;
+    }
+  }
+  if (!have_ex) {
+    Vec3 e{1, 0, 0};
+    ex = sub(e, scale(ez, dot(e, ez)));
+    if (norm(ex) < 0.5) {
+      e = {0, 1, 0};
+      ex = sub(e, scale(ez, dot(e, ez)));
+    }
+    ex = scale(ex, 1.0 / norm(ex));
+  }
+  const Vec3 ey = cross(ez, ex);
+  const Vec3 axes[3] = {ex, ey, ez};
+  for (int c = 0; c < 3; ++c) {
+    g.R[c * 3 + 0] = c == 0 ? axes[0].x : (c == 1 ? axes[0].y : axes[0].z);
+    g.R[c * 3 + 1] = c == 0 ? axes[1].x : (c == 1 ? axes[1].y : axes[1].z);
+    g.R[c * 3 + 2] = c == 0 ? axes[2].x : (c == 1 ? axes[2].y : axes[2].z);
+  }
+  g.M[0] = M.x; g.M[1] = M.y; g.M[2] = M.z;
+  g.a = a;
+  g.A = key.A; g.B = key.B; g.C = key.C;
+  g.n_mu = sp.n_mu; g.n_nu = sp.n_nu; g.n_phi = sp.n_phi;
+  g.q_mu = sp.q_mu; g.q_nu = sp.q_nu; g.q_phi = sp.q_phi; g.n_sp = sp.n_sp;
+  // cell edges (eqs 7, 12, 17)
+  std::vector<double> mu(sp.n_mu + 1), nu(sp.n_nu + 1), ph(sp.n_phi + 1);
+  const double C1 = 2.3 * std::pow(a, 0.25);
+  for (int i = 0; i <= sp.n_mu; ++i) mu[i] = C1 * std::atanh(i / (sp.n_mu + 1.0));
+  for (int i = 0; i <= sp.n_nu; ++i) nu[i] = M_PI * i / sp.n_nu;
+  for (int i = 0; i <= sp.n_phi; ++i) ph[i] = 2.0 * M_PI * i / sp.n_phi;
+  g.n_touch = 0;
+  if (key.C >= 0) {
+    if (sp.n_mu < 2 || sp.n_nu < 2)
+      return fail(PSQ_ERR_ARG, "a refined grid needs n_mu >= 2 and n_nu >= 2");
+    g.RC[0] = RC.x; g.RC[1] = RC.y; g.RC[2] = RC.z;
+    const Vec3 v = sub(RC, M);
+    const double xc = dot(v, ex), yc = dot(v, ey), zc = dot(v, ez);
+    const double rho = std::hypot(xc, yc);
+    const double rA = std::hypot(rho, zc - a), rB = std::hypot(rho, zc + a);
+    const double mu_c = std::acosh(std::max(1.0, (rA + rB) / (2 * a)));
+    const double nu_c = std::acos(std::min(1.0, std::max(-1.0, (rB - rA) / (2 * a))));
+    if (mu_c < mu[sp.n_mu]) {
+      const bool on_axis = rho <= kOnAxisTol * a;
+      if (on_axis && std::fabs(zc) < a) {
+        g.t_mu0 = g.t_mu1 = 0;
+      } else {
+        int best = 1;
+        for (int i = 2; i <= sp.n_mu - 1; ++i)
+          if (std::fabs(mu[i] - mu_c) < std::fabs(mu[best] - mu_c)) best = i;
+        mu[best] = mu_c;
+        g.t_mu0 = best - 1;
+        g.t_mu1 = best;
+      }
+      if (on_axis && std::fabs(zc) >= a) {
+        g.t_nu0 = g.t_nu1 = zc > 0 ? 0 : sp.n_nu - 1;
+      } else {
+        int best = 1;
+        for (int i = 2; i <= sp.n_nu - 1; ++i)
+          if (std::fabs(nu[i] - nu_c) < std::fabs(nu[best] - nu_c)) best = i;
+        nu[best] = nu_c;
+        g.t_nu0 = best - 1;
+        g.t_nu1 = best;
+      }
+      g.t_phi_all = on_axis ? 1 : 0;
+      const int nph = on_axis ? sp.n_phi : (sp.n_phi == 1 ? 1 : 2);
+      g.n_touch = (g.t_mu1 - g.t_mu0 + 1) * (g.t_nu1 - g.t_nu0 + 1) * nph;
+    }
+  }
+  g.edge_off = (int)edges.size();
+  edges.insert(edges.end(), mu.begin(), mu.end());
+  edges.insert(edges.end(), nu.begin(), nu.end());
+  edges.insert(edges.end(), ph.begin(), ph.end());
+  const int64_t q3 = (int64_t)sp.q_mu * sp.q_nu * sp.q_phi;
+  g.K_reg = (int64_t)sp.n_mu * sp.n_nu * sp.n_phi * q3;
+  g.K = g.K_reg + (int64_t)g.n_touch * sp.n_sp * sp.n_sp * sp.n_sp * q3;
+  return PSQ_OK;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
+  P.mask = mask;
+  const int nat = j->nat;
+  // grids: every pair, then every (pair, third centre) when a 3-centre class is asked
+  std::vector<GridKey> keys;
+  for (int A = 0; A < nat; ++A)
+    for (int B = A + 1; B < nat; ++B) keys.push_back({A, B, -1});
+  if ((mask & (PSQ_V | PSQ_J3)) && nat >= 3)
+    for (int A = 0; A < nat; ++A)
+      for (int B = A + 1; B < nat; ++B)
+        for (int C = 0; C < nat; ++C)
+          if (C != A && C != B) keys.push_back({A, B, C});
+  if (mask == 0) keys.clear();
+  std::map<GridKey, int> gidx;
+  for (size_t i = 0; i < keys.size(); ++i) gidx[keys[i]] = (int)i;
+  P.grids.resize(keys.size());
+  for (size_t i = 0; i < keys.size(); ++i) {
+    psq_status st = build_grid(j, keys[i], P.grids[i], P.edges);
+    if (st != PSQ_OK) return st;
+  }
+  // operand rows and shells per grid
+  int64_t ops = 0;  // doubles
+  for (auto& g : P.grids) {
+    const bool refined = g.C >= 0;
+    g.nFA = j->nb[g.A];
+    g.nFB = j->nb[g.B];
+    g.shb_A0 = j->sb0[g.A]; g.shb_A1 = j->sb1[g.A];
+    g.shb_B0 = j->sb0[g.B]; g.shb_B1 = j->sb1[g.B];
+    if (refined) {
+      g.aux_c0 = g.C; g.aux_c1 = -1;
+      g.sha_0 = j->sa0[g.C]; g.sha_1 = j->sa1[g.C]; g.sha_2 = g.sha_3 = 0;
+      g.nG = j->na[g.C];
+    } else {
+      g.aux_c0 = g.A; g.aux_c1 = g.B;
+      g.sha_0 = j->sa0[g.A]; g.sha_1 = j->sa1[g.A];
+      g.sha_2 = j->sa0[g.B]; g.sha_3 = j->sa1[g.B];
+      g.nG = j->na[g.A] + j->na[g.B];
+    }
+    const int nl = g.nFA + g.nFB;
+    int rows = 0;
+    g.row_F = g.row_L = g.row_G = g.row_U = -1;
+    if (!refined) {
+      if (mask & (PSQ_S | PSQ_T | PSQ_V | PSQ_J3)) { g.row_F = rows; rows += nl; }
+      if (mask & PSQ_T) { g.row_L = rows; rows += nl; }
+      if (mask & PSQ_J2) { g.row_G = rows; rows += g.nG; }
+      if (mask & (PSQ_J2 | PSQ_J3)) { g.row_U = rows; rows += g.nG; }
+    } else {
+      g.row_F = rows; rows += nl;
+      if (mask & PSQ_J3) { g.row_U = rows; rows += g.nG; }
+    }
+    g.row_W = rows;
+    rows += 4;
+    g.ld = (int64_t)align_up((size_t)g.K, 32);
+    g.op_off = ops;
+    ops += (int64_t)rows * g.ld;
+    P.n_points += g.K;
+  }
+  // contraction blocks
+  std::vector<int64_t> s_loc(P.grids.size(), -1), t_loc(P.grids.size(), -1), va_loc(P.grids.size(), -1),
+      vb_loc(P.grids.size(), -1), vc_loc(P.grids.size(), -1), j2_loc(P.grids.size(), -1);
+  std::map<std::tuple<int, int, int>, J3Src> j3blk;
+  int64_t res = 0;
+  auto add_block = [&](int g, int a_row, int m, int b_row, int n, int b_mode, int pair_off, int d_row) {
+    GemmBlock b{};
+    b.grid = g; b.a_row = a_row; b.m = m; b.b_row = b_row; b.n = n; b.b_mode = b_mode;
+    b.pair_off = pair_off; b.d_row = d_row; b.res_off = res;
+    res += (int64_t)m * n;
+    P.gblocks.push_back(b);
+    return b.res_off;
+  };
+  for (size_t gi = 0; gi < P.grids.size(); ++gi) {
+    DevGrid& g = P.grids[gi];
+    const int nl = g.nFA + g.nFB;
+    const int w = g.row_W;
+    const int gint = (int)gi;
+    if (g.C < 0) {
+      if (nl > 0) {
+        if (mask & PSQ_S) s_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w);
+        if (mask & PSQ_T) t_loc[gi] = add_block(gint, g.row_F, nl, g.row_L, nl, 0, 0, w);
+        if (mask & PSQ_V) {
+          va_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 1);
+          vb_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 2);
+        }
+      }
+      if ((mask & PSQ_J2) && g.nG > 0) j2_loc[gi] = add_block(gint, g.row_U, g.nG, g.row_G, g.nG, 0, 0, w);
+      if (mask & PSQ_J3) {
+        const int atoms2[2] = {g.A, g.B};
+        for (int xi = 0; xi < 2; ++xi) {
+          const int X = atoms2[xi];
+          if (j->na[X] == 0) continue;
+          const int aoff = xi == 0 ? 0 : j->na[g.A];
+          const int yw[3][2] = {{g.A, g.A}, {g.A, g.B}, {g.B, g.B}};
+          for (auto& p : yw) {
+            const int Y = p[0], W = p[1];
+            if (j->nb[Y] == 0 || j->nb[W] == 0) continue;
+            const GridKey k = grid_for(j, Y, W, X);
+            if (k.A != g.A || k.B != g.B || k.C != -1) continue;
+            const int yoff = Y == g.A ? 0 : g.nFA, woff = W == g.A ? 0 : g.nFA;
+            const int pair_off = (int)P.pairs.size();
+            if (Y != W) {
+              for (int i = 0; i < j->nb[Y]; ++i)
+                for (int jj = 0; jj < j->nb[W]; ++jj) P.pairs.push_back(make_short2(yoff + i, woff + jj));
+            } else {
+              for (int i = 0; i < j->nb[Y]; ++i)
+                for (int jj = i; jj < j->nb[Y]; ++jj) P.pairs.push_back(make_short2(yoff + i, yoff + jj));
+            }
+            const int np = (int)P.pairs.size() - pair_off;
+            const int64_t off = add_block(gint, g.row_U + aoff, j->na[X], g.row_F, np, 1, pair_off, w);
+            j3blk[{X, Y, W}] = J3Src{off, np, j->nb[W], Y == W ? 1 : 0, 0};
+          }
+        }
+      }
+    } else {
+      if ((mask & PSQ_V) && g.nFA > 0 && g.nFB > 0)
+        vc_loc[gi] = add_block(gint, g.row_F, g.nFA, g.row_F + g.nFA, g.nFB, 0, 0, w + 3);
+      if ((mask & PSQ_J3) && j->na[g.C] > 0 && g.nFA > 0 && g.nFB > 0) {
+        const int pair_off = (int)P.pairs.size();
+        for (int i = 0; i < g.nFA; ++i)
+          for (int jj = 0; jj < g.nFB; ++jj) P.pairs.push_back(make_short2(i, g.nFA + jj));
+        const int np = g.nFA * g.nFB;
+        const int64_t off = add_block(gint, g.row_U, j->na[g.C], g.row_F, np, 1, pair_off, w);
+        j3blk[{g.C, g.A, g.B}] = J3Src{off, np, g.nFB, 0, 0};
+      }
+    }
+  }
+  // chunking: enough CTAs for several waves, chunks of at least 2048 points
+  int64_t tiles = 0;
+  for (auto& b : P.gblocks) tiles += (int64_t)((b.m + kTile - 1) / kTile) * ((b.n + kTile - 1) / kTile);
+  const int64_t want = 2LL * kSmCount * 8;
+  const int cglob = (int)std::max<int64_t>(1, tiles > 0 ? (want + tiles - 1) / tiles : 1);
+  int64_t part = 0;
+  for (size_t bi = 0; bi < P.gblocks.size(); ++bi) {
+    GemmBlock& b = P.gblocks[bi];
+    const int64_t K = P.grids[b.grid].K;
+    b.n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(cglob, (K + 2047) / 2048));
+    b.part_off = part;
+    part += (int64_t)b.n_chunks * b.m * b.n;
+    const int tm = (b.m + kTile - 1) / kTile, tn = (b.n + kTile - 1) / kTile;
+    for (int c = 0; c < b.n_chunks; ++c)
+      for (int x = 0; x < tm; ++x)
+        for (int y = 0; y < tn; ++y) P.items.push_back(GemmItem{(int)bi, x, y, c});
+  }
+  P.elem_begin.resize(P.gblocks.size() + 1);
+  P.elem_begin[0] = 0;
+  for (size_t bi = 0; bi < P.gblocks.size(); ++bi)
+    P.elem_begin[bi + 1] = P.elem_begin[bi] + (int64_t)P.gblocks[bi].m * P.gblocks[bi].n;
+  for (size_t gi = 0; gi < P.grids.size(); ++gi)
+    for (int64_t p0 = 0; p0 < P.grids[gi].K; p0 += kPointsPerBlock) P.pblocks.push_back(PointBlock{(int)gi, 0, p0});
+  // assembly sources (S, T, V, J2 in slots 0..3)
+  auto local_off = [&](const DevGrid& g, int X) { return X == g.A ? 0 : g.nFA; };
+  auto aux_off = [&](const DevGrid& g, int X) { return X == g.A ? 0 : j->na[g.A]; };
+  for (int c = 0; c < 4; ++c) P.src_ptr[c].assign(nat * nat + 1, 0);
+  for (int X = 0; X < nat; ++X) {
+    for (int Y = 0; Y < nat; ++Y) {
+      for (int c = 0; c < 4; ++c) P.src_ptr[c][X * nat + Y] = (int)P.src[c].size();
+      if (X > Y || mask == 0) continue;
+      const GridKey kb = grid_for(j, X, Y, X);
+      const int gb = gidx[kb];
+      const DevGrid& G = P.grids[gb];
+      const int nl = G.nFA + G.nFB;
+      if (mask & PSQ_S) P.src[0].push_back(SrcEntry{s_loc[gb], nl, local_off(G, X), local_off(G, Y), 1.0});
+      if (mask & PSQ_T) P.src[1].push_back(SrcEntry{t_loc[gb], nl, local_off(G, X), local_off(G, Y), 1.0});
+      if (mask & PSQ_V) {
+        for (int C = 0; C < nat; ++C) {
+          const GridKey k = grid_for(j, X, Y, C);
+          const int gv = gidx[k];
+          const DevGrid& H = P.grids[gv];
+          const double z = -(double)j->atoms[C].Z;
+          if (k.C >= 0) {
+            P.src[2].push_back(SrcEntry{vc_loc[gv], H.nFB, 0, 0, z});
+          } else {
+            const int64_t off = C == H.A ? va_loc[gv] : vb_loc[gv];
+            P.src[2].push_back(SrcEntry{off, H.nFA + H.nFB, local_off(H, X), local_off(H, Y), z});
+          }
+        }
+      }
+      if (mask & PSQ_J2) P.src[3].push_back(SrcEntry{j2_loc[gb], G.nG, aux_off(G, X), aux_off(G, Y), 1.0});
+    }
+  }
+  for (int c = 0; c < 4; ++c) P.src_ptr[c][nat * nat] = (int)P.src[c].size();
+  P.j3.assign((size_t)nat * nat * nat, J3Src{0, 0, 0, 0, 0});
+  for (auto& kv : j3blk) {
+    const int X = std::get<0>(kv.first), Y = std::get<1>(kv.first), W = std::get<2>(kv.first);
+    P.j3[((size_t)X * nat + Y) * nat + W] = kv.second;
+  }
+  // useful contractions: for every molecule-matrix block, rows x cols x the live points of
+  // the one grid that integrates it (same-atom blocks count i <= j once)
+  P.contractions = 0;
+  auto live = [&](GridKey k) {
+    const DevGrid& g = P.grids[gidx[k]];
+    return (double)(g.K - (int64_t)g.n_touch * g.q_mu * g.q_nu * g.q_phi);
+  };
+  if (mask) {
+    for (int A = 0; A < nat; ++A)
+      for (int B = A; B < nat; ++B) {
+        const double nab = A != B ? (double)j->nb[A] * j->nb[B] : 0.5 * j->nb[A] * (j->nb[A] + 1.0);
+        if (mask & PSQ_S) P.contractions += nab * live(grid_for(j, A, B, A));
+        if (mask & PSQ_T) P.contractions += nab * live(grid_for(j, A, B, A));
+        for (int C = 0; C < nat; ++C) {
+          if (mask & PSQ_V) P.contractions += nab * live(grid_for(j, A, B, C));
+          if (mask & PSQ_J3) P.contractions += j->na[C] * nab * live(grid_for(j, A, B, C));
+        }
+        if (mask & PSQ_J2) {
+          const double ncd = A != B ? (double)j->na[A] * j->na[B] : 0.5 * j->na[A] * (j->na[A] + 1.0);
+          P.contractions += ncd * live(grid_for(j, A, B, A));
+        }
+      }
+  }
+  int nclasses = 0;
+  for (int c = 0; c < 5; ++c) nclasses += (mask >> c) & 1;
+  P.launches = P.grids.empty() ? 0 : 3 + nclasses;
+  // table layout
+  size_t off = 0;
+  auto sec = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  P.o_grids = sec(sizeof(DevGrid) * P.grids.size());
+  P.o_edges = sec(sizeof(double) * P.edges.size());
+  P.o_bsh = sec(sizeof(DevShell) * j->dbs.size());
+  P.o_ash = sec(sizeof(DevShell) * j->das.size());
+  P.o_xyz = sec(sizeof(double) * 3 * nat);
+  P.o_pb = sec(sizeof(PointBlock) * P.pblocks.size());
+  P.o_gb = sec(sizeof(GemmBlock) * P.gblocks.size());
+  P.o_it = sec(sizeof(GemmItem) * P.items.size());
+  P.o_pairs = sec(sizeof(short2) * P.pairs.size());
+  P.o_eb = sec(sizeof(int64_t) * P.elem_begin.size());
+  P.o_fa = sec(sizeof(int) * j->fn_atom.size());
+  P.o_fl = sec(sizeof(int) * j->fn_local.size());
+  P.o_aa = sec(sizeof(int) * j->aux_atom.size());
+  P.o_al = sec(sizeof(int) * j->aux_local.size());
+  for (int c = 0; c < 4; ++c) {
+    P.o_src[c] = sec(sizeof(SrcEntry) * P.src[c].size());
+    P.o_ptr[c] = sec(sizeof(int) * P.src_ptr[c].size());
+  }
+  P.o_j3 = sec(sizeof(J3Src) * P.j3.size());
+  P.table_bytes = off;
+  P.ops_off = off;
+  off = align_up(off + sizeof(double) * (size_t)ops, 256);
+  P.part_off = off;
+  off = align_up(off + sizeof(double) * (size_t)part, 256);
+  P.res_off = off;
+  off = align_up(off + sizeof(double) * (size_t)res, 256);
+  P.ws_bytes = off;
+  // staging copy of the tables (page-locked when the context has a device)
+  P.pinned = j->ctx->device >= 0;
+  if (P.pinned) {
+    if (cudaMallocHost((void**)&P.staging, std::max<size_t>(P.table_bytes, 256)) != cudaSuccess) {
+      P.staging = nullptr;
+      return fail(PSQ_ERR_OOM, "cudaMallocHost of %zu bytes failed", P.table_bytes);
+    }
+  } else {
+    P.staging = (double*)std::malloc(std::max<size_t>(P.table_bytes, 256));
+    if (!P.staging) return fail(PSQ_ERR_OOM, "malloc of %zu bytes failed", P.table_bytes);
+  }
+  char* s = (char*)P.staging;
+  std::memset(s, 0, P.table_bytes);
+  auto put = [&](size_t o, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(s + o, src, bytes);
+  };
+  put(P.o_grids, P.grids.data(), sizeof(DevGrid) * P.grids.size());
+  put(P.o_edges, P.edges.data(), sizeof(double) * P.edges.size());
+  put(P.o_bsh, j->dbs.data(), sizeof(DevShell) * j->dbs.size());
+  put(P.o_ash, j->das.data(), sizeof(DevShell) * j->das.size());
+  std::vector<double> xyz(3 * nat);
+  for (int X = 0; X < nat; ++X)
+    for (int c = 0; c < 3; ++c) xyz[3 * X + c] = j->atoms[X].xyz[c];
+  put(P.o_xyz, xyz.data(), sizeof(double) * xyz.size());
+  put(P.o_pb, P.pblocks.data(), sizeof(PointBlock) * P.pblocks.size());
+  put(P.o_gb, P.gblocks.data(), sizeof(GemmBlock) * P.gblocks.size());
+  put(P.o_it, P.items.data(), sizeof(GemmItem) * P.items.size());
+  put(P.o_pairs, P.pairs.data(), sizeof(short2) * P.pairs.size());
+  put(P.o_eb, P.elem_begin.data(), sizeof(int64_t) * P.elem_begin.size());
+  put(P.o_fa, j->fn_atom.data(), sizeof(int) * j->fn_atom.size());
+  put(P.o_fl, j->fn_local.data(), sizeof(int) * j->fn_local.size());
+  put(P.o_aa, j->aux_atom.data(), sizeof(int) * j->aux_atom.size());
+  put(P.o_al, j->aux_local.data(), sizeof(int) * j->aux_local.size());
+  for (int c = 0; c < 4; ++c) {
+    put(P.o_src[c], P.src[c].data(), sizeof(SrcEntry) * P.src[c].size());
+    put(P.o_ptr[c], P.src_ptr[c].data(), sizeof(int) * P.src_ptr[c].size());
+  }
+  put(P.o_j3, P.j3.data(), sizeof(J3Src) * P.j3.size());
+  return PSQ_OK;
+}
+
+psq_status get_plan(psq_job* j, unsigned mask, Plan** out) {
+  std::lock_guard<std::mutex> lk(j->mu);
+  auto it = j->plans.find(mask);
+  if (it != j->plans.end()) {
+    *out = it->second.get();
+    return PSQ_OK;
+  }
+  std::unique_ptr<Plan> p(new (std::nothrow) Plan());
+  if (!p) return fail(PSQ_ERR_OOM, "plan allocation failed");
+  psq_status st = make_plan(j, mask, *p);
+  if (st != PSQ_OK) return st;
+  *out = p.get();
+  j->plans[mask] = std::move(p);
+  return PSQ_OK;
+}
+
+// Records a timing event before a launch of `kind` (kind -1 closes a psq_compute call).
+cudaError_t mark(psq_job* j, int kind, cudaStream_t s) {
+  if (!j->prof_on || j->prof.size() >= (1u << 20)) return cudaSuccess;
+  cudaEvent_t e;
+  if (!j->ev_free.empty()) {
+    e = j->ev_free.back();
+    j->ev_free.pop_back();
+  } else {
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+  }
+  j->prof.push_back({kind, e});
+  return cudaEventRecord(e, s);
+}
+
+LaunchTables tables_at(const Plan& P, char* ws) {
+  LaunchTables t{};
+  t.grids = (const DevGrid*)(ws + P.o_grids);
+  t.edges = (const double*)(ws + P.o_edges);
+  t.bshell = (const DevShell*)(ws + P.o_bsh);
+  t.ashell = (const DevShell*)(ws + P.o_ash);
+  t.atom_xyz = (const double*)(ws + P.o_xyz);
+  t.pblocks = (const PointBlock*)(ws + P.o_pb);
+  t.n_pblocks = (int)P.pblocks.size();
+  t.gblocks = (const GemmBlock*)(ws + P.o_gb);
+  t.n_gblocks = (int)P.gblocks.size();
+  t.items = (const GemmItem*)(ws + P.o_it);
+  t.n_items = (int)P.items.size();
+  t.pairs = (const short2*)(ws + P.o_pairs);
+  t.elem_begin = (const int64_t*)(ws + P.o_eb);
+  t.n_elems = P.elem_begin.empty() ? 0 : P.elem_begin.back();
+  return t;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char* psq_last_error(void) { return g_err.c_str(); }
+
+psq_status psq_context_create(int device, psq_context** out) {
+  if (!out) return fail(PSQ_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (device == -1) {  // planning only: jobs can be created and queried, not computed
+    psq_context* c = new (std::nothrow) psq_context{-1};
+    if (!c) return fail(PSQ_ERR_OOM, "context allocation failed");
+    *out = c;
+    return PSQ_OK;
+  }
+  int n = 0;
+  CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(PSQ_ERR_ARG, "device %d of %d", device, n);
+  CUDA_TRY(cudaSetDevice(device));
+  double x[(kMaxQ + 1) * kMaxQ] = {0}, w[(kMaxQ + 1) * kMaxQ] = {0};
+  for (int q = 1; q <= kMaxQ; ++q) gauss_legendre(q, x + q * kMaxQ, w + q * kMaxQ);
+  double klm[(kMaxL + 1) * (kMaxL + 1)];
+  for (int l = 0; l <= kMaxL; ++l)
+    for (int m = -l; m <= l; ++m) {
+      const int am = std::abs(m);
+      double k = std::sqrt((2 * l + 1) / (4 * M_PI) * factorial(l - am) / factorial(l + am));
+      if (m != 0) k *= std::sqrt(2.0);
+      klm[l * l + l + m] = k;
+    }
+  upload_gl_tables(x, w, klm);
+  CUDA_TRY(cudaGetLastError());
+  psq_context* c = new (std::nothrow) psq_context{device};
+  if (!c) return fail(PSQ_ERR_OOM, "context allocation failed");
+  *out = c;
+  return PSQ_OK;
+}
+
+psq_status psq_context_destroy(psq_context* ctx) {
+  delete ctx;
+  return PSQ_OK;
+}
+
+psq_status psq_job_create(psq_context* ctx, const psq_atom* atoms, int n_atoms, const psq_shell* basis,
+                          int n_basis_shells, const psq_shell* aux, int n_aux_shells,
+                          const psq_grid_spec* pair_specs, int n_specs, psq_precision precision,
+                          psq_job** out) {
+  if (!out) return fail(PSQ_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !atoms || (!basis && n_basis_shells) || (!aux && n_aux_shells) || !pair_specs)
+    return fail(PSQ_ERR_ARG, "NULL argument");
+  if (n_atoms < 2) return fail(PSQ_ERR_UNSUPPORTED, "a job needs at least two atoms (got %d)", n_atoms);
+  if (n_basis_shells < 0 || n_aux_shells < 0) return fail(PSQ_ERR_ARG, "negative shell count");
+  const int npairs = n_atoms * (n_atoms - 1) / 2;
+  if (n_specs != 1 && n_specs != npairs)
+    return fail(PSQ_ERR_ARG, "n_specs must be 1 or n_atoms*(n_atoms-1)/2 = %d (got %d)", npairs, n_specs);
+  if (precision != PSQ_FP64 && precision != PSQ_MIXED) return fail(PSQ_ERR_ARG, "unknown precision");
+  for (int i = 0; i < n_atoms; ++i) {
+    if (atoms[i].Z < 0 || atoms[i].Z > 200) return fail(PSQ_ERR_ARG, "atom %d: Z = %d", i, atoms[i].Z);
+    for (int c = 0; c < 3; ++c)
+      if (!std::isfinite(atoms[i].xyz[c])) return fail(PSQ_ERR_ARG, "atom %d: position not finite", i);
+  }
+  for (int i = 0; i < n_atoms; ++i)
+    for (int k = i + 1; k < n_atoms; ++k) {
+      const double dx = atoms[i].xyz[0] - atoms[k].xyz[0], dy = atoms[i].xyz[1] - atoms[k].xyz[1],
+                   dz = atoms[i].xyz[2] - atoms[k].xyz[2];
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) < 1e-6)
+        return fail(PSQ_ERR_GEOMETRY, "atoms %d and %d coincide", i, k);
+    }
+  auto check_shells = [&](const psq_shell* s, int n, const char* what) -> psq_status {
+    for (int i = 0; i < n; ++i) {
+      if (s[i].atom < 0 || s[i].atom >= n_atoms) return fail(PSQ_ERR_ARG, "%s shell %d: atom %d", what, i, s[i].atom);
+      if (i > 0 && s[i].atom < s[i - 1].atom)
+        return fail(PSQ_ERR_ARG, "%s shells must be grouped by atom in ascending order", what);
+      if (s[i].n < 1 || s[i].l < 0 || s[i].l >= s[i].n)
+        return fail(PSQ_ERR_ARG, "%s shell %d: n = %d, l = %d (need n > l >= 0)", what, i, s[i].n, s[i].l);
+      if (s[i].l > kMaxL || s[i].n > kMaxN)
+        return fail(PSQ_ERR_UNSUPPORTED, "%s shell %d: l = %d, n = %d (max l %d, n %d)", what, i, s[i].l, s[i].n,
+                    kMaxL, kMaxN);
+      if (!(s[i].zeta > 0) || !std::isfinite(s[i].zeta))
+        return fail(PSQ_ERR_ARG, "%s shell %d: zeta = %g", what, i, s[i].zeta);
+    }
+    return PSQ_OK;
+  };
+  psq_status st = check_shells(basis, n_basis_shells, "basis");
+  if (st != PSQ_OK) return st;
+  st = check_shells(aux, n_aux_shells, "aux");
+  if (st != PSQ_OK) return st;
+  for (int i = 0; i < n_specs; ++i) {
+    const psq_grid_spec& s = pair_specs[i];
+    if (s.n_mu < 1 || s.n_nu < 1 || s.n_phi < 1 || s.n_sp < 1)
+      return fail(PSQ_ERR_ARG, "grid spec %d: cell counts and n_sp must be >= 1", i);
+    if (s.q_mu < 1 || s.q_nu < 1 || s.q_phi < 1 || s.q_mu > kMaxQ || s.q_nu > kMaxQ || s.q_phi > kMaxQ)
+      return fail(PSQ_ERR_UNSUPPORTED, "grid spec %d: Q must be within 1..%d", i, kMaxQ);
+    if ((int64_t)s.n_mu * s.n_nu * s.n_phi * s.q_mu * s.q_nu * s.q_phi > (int64_t)1 << 31)
+      return fail(PSQ_ERR_UNSUPPORTED, "grid spec %d: more than 2^31 points", i);
+  }
+  psq_job* j = new (std::nothrow) psq_job();
+  if (!j) return fail(PSQ_ERR_OOM, "job allocation failed");
+  j->ctx = ctx;
+  j->nat = n_atoms;
+  j->atoms.assign(atoms, atoms + n_atoms);
+  j->basis.assign(basis, basis + n_basis_shells);
+  j->aux.assign(aux, aux + n_aux_shells);
+  j->specs.assign(pair_specs, pair_specs + n_specs);
+  j->prec = precision;
+  auto layout = [&](const std::vector<psq_shell>& sh, std::vector<int>& cnt, std::vector<int>& s0,
+                    std::vector<int>& s1, std::vector<int>& fatom, std::vector<int>& flocal,
+                    std::vector<DevShell>& dsh) {
+    cnt.assign(n_atoms, 0);
+    s0.assign(n_atoms, (int)sh.size());
+    s1.assign(n_atoms, (int)sh.size());
+    for (size_t i = 0; i < sh.size(); ++i) {
+      const int X = sh[i].atom;
+      if (s0[X] == (int)sh.size()) s0[X] = (int)i;
+      s1[X] = (int)i + 1;
+      DevShell d{};
+      d.n = sh[i].n;
+      d.l = sh[i].l;
+      d.atom = X;
+      d.fn0 = cnt[X];
+      d.zeta = sh[i].zeta;
+      d.norm = std::pow(2.0 * sh[i].zeta, sh[i].n + 0.5) / std::sqrt(factorial(2 * sh[i].n));
+      dsh.push_back(d);
+      for (int m = 0; m < 2 * sh[i].l + 1; ++m) {
+        fatom.push_back(X);
+        flocal.push_back(cnt[X] + m);
+      }
+      cnt[X] += 2 * sh[i].l + 1;
+    }
+    for (int X = 0; X < n_atoms; ++X)
+      if (s1[X] < s0[X] || s0[X] == (int)sh.size()) s0[X] = s1[X] = 0;
+  };
+  layout(j->basis, j->nb, j->sb0, j->sb1, j->fn_atom, j->fn_local, j->dbs);
+  layout(j->aux, j->na, j->sa0, j->sa1, j->aux_atom, j->aux_local, j->das);
+  j->nbf = (int)j->fn_atom.size();
+  j->naux = (int)j->aux_atom.size();
+  j->nn.assign(n_atoms, 0);
+  for (int X = 0; X < n_atoms; ++X) {
+    int best = -1;
+    double bd = 0;
+    for (int Y = 0; Y < n_atoms; ++Y) {
+      if (Y == X) continue;
+      const double d = norm(sub(pos(j, X), pos(j, Y)));
+      if (best < 0 || d < bd) { best = Y; bd = d; }
+    }
+    j->nn[X] = best;
+  }
+  if (precision == PSQ_MIXED) {
+    delete j;
+    return fail(PSQ_ERR_UNSUPPORTED, "mixed precision is not built in this library");
+  }
+  *out = j;
+  return PSQ_OK;
+}
+
+psq_status psq_job_destroy(psq_job* job) {
+  delete job;
+  return PSQ_OK;
+}
+
+psq_status psq_job_sizes(const psq_job* job, int* n_bf, int* n_aux) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  if (n_bf) *n_bf = job->nbf;
+  if (n_aux) *n_aux = job->naux;
+  return PSQ_OK;
+}
+
+psq_status psq_job_workspace(const psq_job* job, unsigned mask, size_t* bytes) {
+  if (!job || !bytes) return fail(PSQ_ERR_ARG, "NULL argument");
+  if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
+  Plan* P = nullptr;
+  psq_status st = get_plan(const_cast<psq_job*>(job), mask, &P);
+  if (st != PSQ_OK) return st;
+  *bytes = P->ws_bytes;
+  return PSQ_OK;
+}
+
+psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_t* n_points,
+                         double* contractions, int* launches) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
+  Plan* P = nullptr;
+  psq_status st = get_plan(const_cast<psq_job*>(job), mask, &P);
+  if (st != PSQ_OK) return st;
+  if (n_grids) *n_grids = (int)P->grids.size();
+  if (n_points) *n_points = P->n_points;
+  if (contractions) *contractions = P->contractions;
+  if (launches) *launches = P->launches;
+  return PSQ_OK;
+}
+
+psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
+                       void* stream) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  if (job->ctx->device < 0) return fail(PSQ_ERR_ARG, "the job's context has no device (planning only)");
+  if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
+  if (mask == 0) return PSQ_OK;
+  if (!d_out) return fail(PSQ_ERR_ARG, "d_out is NULL");
+  for (int c = 0; c < 5; ++c)
+    if ((mask >> c) & 1 && !d_out[c]) return fail(PSQ_ERR_ARG, "output %d is NULL", c);
+  Plan* P = nullptr;
+  psq_status st = get_plan(job, mask, &P);
+  if (st != PSQ_OK) return st;
+  if (!d_workspace || ws_bytes < P->ws_bytes)
+    return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->ws_bytes);
+  if ((uintptr_t)d_workspace % 256) return fail(PSQ_ERR_ARG, "workspace must be 256-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)d_workspace;
+  CUDA_TRY(mark(job, 0, s));
+  CUDA_TRY(cudaMemcpyAsync(ws, P->staging, P->table_bytes, cudaMemcpyHostToDevice, s));
+  const LaunchTables t = tables_at(*P, ws);
+  double* ops = (double*)(ws + P->ops_off);
+  double* part = (double*)(ws + P->part_off);
+  double* res = (double*)(ws + P->res_off);
+  CUDA_TRY(mark(job, 1, s));
+  CUDA_TRY(launch_eval_fp64(t, ops, 0, s));
+  CUDA_TRY(mark(job, 2, s));
+  CUDA_TRY(launch_contract_fp64(t, ops, part, s));
+  CUDA_TRY(mark(job, 3, s));
+  CUDA_TRY(launch_reduce(t, part, res, s));
+  CUDA_TRY(mark(job, 4, s));
+  const int* fa = (const int*)(ws + P->o_fa);
+  const int* fl = (const int*)(ws + P->o_fl);
+  const int* aa = (const int*)(ws + P->o_aa);
+  const int* al = (const int*)(ws + P->o_al);
+  const unsigned cls[4] = {PSQ_S, PSQ_T, PSQ_V, PSQ_J2};
+  for (int c = 0; c < 4; ++c) {
+    if (!(mask & cls[c])) continue;
+    const int n = c == 3 ? job->naux : job->nbf;
+    const int* at = c == 3 ? aa : fa;
+    const int* lo = c == 3 ? al : fl;
+    CUDA_TRY(launch_assemble((int)cls[c], job->nat, n, 0, at, lo, nullptr, nullptr,
+                             (const SrcEntry*)(ws + P->o_src[c]), (const int*)(ws + P->o_ptr[c]), nullptr, res,
+                             d_out[c], s));
+  }
+  if (mask & PSQ_J3)
+    CUDA_TRY(launch_assemble(16, job->nat, job->nbf, job->naux, fa, fl, aa, al, nullptr, nullptr,
+                             (const J3Src*)(ws + P->o_j3), res, d_out[4], s));
+  CUDA_TRY(mark(job, -1, s));
+  return PSQ_OK;
+}
+
+psq_status psq_profile_enable(psq_job* job, int on) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  job->prof_on = on != 0;
+  return PSQ_OK;
+}
+
+psq_status psq_profile_read(psq_job* job, double ms[8], int counts[8]) {
+  if (!job || !ms || !counts) return fail(PSQ_ERR_ARG, "NULL argument");
+  for (int k = 0; k < 8; ++k) { ms[k] = 0; counts[k] = 0; }
+  for (size_t i = 0; i < job->prof.size(); ++i) {
+    CUDA_TRY(cudaEventSynchronize(job->prof[i].ev));
+  }
+  for (size_t i = 0; i + 1 < job->prof.size(); ++i) {
+    const int k = job->prof[i].kind;
+    if (k < 0 || k >= 8) continue;
+    float dt = 0;
+    CUDA_TRY(cudaEventElapsedTime(&dt, job->prof[i].ev, job->prof[i + 1].ev));
+    ms[k] += dt;
+    counts[k] += 1;
+  }
+  for (auto& r : job->prof) job->ev_free.push_back(r.ev);
+  job->prof.clear();
+  return PSQ_OK;
+}
+
+psq_status psq_job_io_bytes(const psq_job* job, unsigned mask, size_t* h2d, size_t* d2h) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
+  Plan* P = nullptr;
+  psq_status st = get_plan(const_cast<psq_job*>(job), mask, &P);
+  if (st != PSQ_OK) return st;
+  size_t out = 0;
+  const size_t nb = job->nbf, na = job->naux;
+  if (mask & PSQ_S) out += nb * nb;
+  if (mask & PSQ_T) out += nb * nb;
+  if (mask & PSQ_V) out += nb * nb;
+  if (mask & PSQ_J2) out += na * na;
+  if (mask & PSQ_J3) out += na * nb * nb;
+  if (h2d) *h2d = P->table_bytes;
+  if (d2h) *d2h = out * sizeof(double);
+  return PSQ_OK;
+}
+
+psq_status psq_compute_host(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
+                            double* h_out[5], void* stream) {
+  psq_status st = psq_compute(job, mask, d_workspace, ws_bytes, d_out, stream);
+  if (st != PSQ_OK) return st;
+  if (!h_out) return fail(PSQ_ERR_ARG, "h_out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int c = 0; c < 5; ++c) {
+    if (!((mask >> c) & 1)) continue;
+    if (!h_out[c]) return fail(PSQ_ERR_ARG, "host output %d is NULL", c);
+    size_t n = c < 3 ? (size_t)job->nbf * job->nbf
+                     : (c == 3 ? (size_t)job->naux * job->naux : (size_t)job->naux * job->nbf * job->nbf);
+    CUDA_TRY(cudaMemcpyAsync(h_out[c], d_out[c], n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PSQ_OK;
+}
+
+psq_status psq_job_grid_info(const psq_job* job, int g, int* A, int* B, int* C, int64_t* n_points) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  Plan* P = nullptr;
+  psq_status st = get_plan(const_cast<psq_job*>(job), PSQ_ALL, &P);
+  if (st != PSQ_OK) return st;
+  if (g < 0 || g >= (int)P->grids.size()) return fail(PSQ_ERR_ARG, "grid %d of %zu", g, P->grids.size());
+  if (A) *A = P->grids[g].A;
+  if (B) *B = P->grids[g].B;
+  if (C) *C = P->grids[g].C;
+  if (n_points) *n_points = P->grids[g].K;
+  return PSQ_OK;
+}
+
+psq_status psq_job_grid_points(psq_job* job, int g, void* d_workspace, size_t ws_bytes, double* d_out,
+                               void* stream) {
+  if (!job || !d_out) return fail(PSQ_ERR_ARG, "NULL argument");
+  if (job->ctx->device < 0) return fail(PSQ_ERR_ARG, "the job's context has no device (planning only)");
+  Plan* P = nullptr;
+  psq_status st = get_plan(job, PSQ_ALL, &P);
+  if (st != PSQ_OK) return st;
+  if (g < 0 || g >= (int)P->grids.size()) return fail(PSQ_ERR_ARG, "grid %d of %zu", g, P->grids.size());
+  if (!d_workspace || ws_bytes < P->table_bytes)
+    return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->table_bytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)d_workspace;
+  CUDA_TRY(cudaMemcpyAsync(ws, P->staging, P->table_bytes, cudaMemcpyHostToDevice, s));
+  LaunchTables t = tables_at(*P, ws);
+  t.n_elems = P->grids[g].K;
+  CUDA_TRY(launch_grid_points(t, g, d_out, s));
+  return PSQ_OK;
+}
+
+psq_status psq_job_grid_functions(psq_job* job, int g, int kind, void* d_workspace, size_t ws_bytes,
+                                  double* d_out, int* rows, void* stream) {
+  if (!job || !d_out) return fail(PSQ_ERR_ARG, "NULL argument");
+  if (job->ctx->device < 0) return fail(PSQ_ERR_ARG, "the job's context has no device (planning only)");
+  if (kind < 0 || kind > 3) return fail(PSQ_ERR_ARG, "kind %d", kind);
+  Plan* P = nullptr;
+  psq_status st = get_plan(job, PSQ_ALL, &P);
+  if (st != PSQ_OK) return st;
+  if (g < 0 || g >= (int)P->grids.size()) return fail(PSQ_ERR_ARG, "grid %d of %zu", g, P->grids.size());
+  // one-grid table: the grid with only the requested rows, written straight into d_out
+  DevGrid G = P->grids[g];
+  G.op_off = 0;
+  G.ld = G.K;
+  G.row_F = G.row_L = G.row_G = G.row_U = G.row_W = -1;
+  int nrows = kind <= 1 ? G.nFA + G.nFB : G.nG;
+  if (kind == 0) G.row_F = 0;
+  if (kind == 1) G.row_L = 0;
+  if (kind == 2) G.row_G = 0;
+  if (kind == 3) G.row_U = 0;
+  if (rows) *rows = nrows;
+  std::vector<PointBlock> pb;
+  for (int64_t p0 = 0; p0 < G.K; p0 += kPointsPerBlock) pb.push_back(PointBlock{0, 0, p0});
+  const size_t o_grid = 0, o_pb = align_up(sizeof(DevGrid), 256);
+  const size_t need = o_pb + align_up(sizeof(PointBlock) * pb.size(), 256);
+  if (!d_workspace || ws_bytes < P->table_bytes + need)
+    return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->table_bytes + need);
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)d_workspace;
+  CUDA_TRY(cudaMemcpyAsync(ws, P->staging, P->table_bytes, cudaMemcpyHostToDevice, s));
+  char* extra = ws + P->table_bytes;
+  CUDA_TRY(cudaMemcpyAsync(extra + o_grid, &G, sizeof(G), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(extra + o_pb, pb.data(), sizeof(PointBlock) * pb.size(), cudaMemcpyHostToDevice, s));
+  LaunchTables t = tables_at(*P, ws);
+  t.grids = (const DevGrid*)(extra + o_grid);
+  t.pblocks = (const PointBlock*)(extra + o_pb);
+  t.n_pblocks = (int)pb.size();
+  CUDA_TRY(launch_eval_fp64(t, d_out, 0, s));
+  CUDA_TRY(cudaStreamSynchronize(s));  // the host copies above live on this stack frame
+  return PSQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal structures shared by the host planner (psq_host.cpp) and the CUDA kernels
+// (psq_kernels.cu, psq_mma.cu).  Everything here is plain data laid out for one H2D copy.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace psq {
+
+constexpr int kMaxL = 6;    // highest angular momentum of a basis or aux shell
+constexpr int kMaxN = 12;   // highest principal quantum number
+constexpr int kMaxQ = 16;   // Gauss-Legendre points per dimension
+constexpr int kTile = 32;   // FP64 contraction output tile (rows and columns)
+
+// One shell of STO or aux functions (eq 1), with its radial normalisation.
+struct DevShell {
+  int n, l, atom, fn0;   // fn0: first function index of the shell within its atom
+  double zeta, norm;     // norm = (2 zeta)^(n+1/2) / sqrt((2n)!)
+};
+
+// One PS grid: a pair (A, B) with A at (0,0,+a) of its own frame, optionally refined around
+// a third centre C (Section 2.2).  Points are numbered: regular cells (i, j, k) x Q^3 nodes,
+// where cells touching C carry zero weight, then the N_SP^3 sub-cells of each touching cell.
+struct DevGrid {
+  double M[3];      // midpoint of A and B (molecule frame)
+  double R[9];      // rotation pair frame -> molecule frame, R[i*3+j] = axis j, component i
+  double RC[3];     // third-centre position (molecule frame), refined grids only
+  double a;         // half the A-B distance
+  int A, B, C;      // atoms; C = -1 for an unrefined grid
+  int n_mu, n_nu, n_phi, q_mu, q_nu, q_phi, n_sp;
+  int edge_off;     // edges: mu[n_mu+1], nu[n_nu+1], phi[n_phi+1] from this offset
+  int t_mu0, t_mu1, t_nu0, t_nu1, t_phi_all, n_touch;  // cells touching C (n_touch = 0: none)
+  int64_t K, K_reg; // points; points of the regular cell block
+  // Operand matrices of this grid: rows of ld doubles (or floats) from op_off.
+  int64_t op_off;
+  int64_t ld;
+  int row_F, row_L, row_G, row_U, row_W;  // first row per kind, -1 when absent
+  int nFA, nFB;     // basis functions of A and of B (rows of F/L: A's then B's)
+  int nG;           // aux rows in G/U (A's then B's on an unrefined grid, C's on a refined one)
+  int shb_A0, shb_A1, shb_B0, shb_B1;     // basis shell ranges of A and B
+  int sha_0, sha_1, sha_2, sha_3;         // aux shells: [0,1) first centre, [2,3) second
+  int aux_c0, aux_c1;                     // atoms of the two aux ranges (-1 none)
+};
+
+// One output block of a contraction (eq 9): out[r][c] = sum_p A_r(p) d(p) B_c(p), where
+// B_c is a row of the grid's operands (b_mode 0) or the product of two basis rows (b_mode 1,
+// the 3-index operand chi_i chi_j of eq 16).
+struct GemmBlock {
+  int grid;
+  int a_row, m;
+  int b_row, n;
+  int b_mode;
+  int pair_off;     // into the pair table (b_mode 1): pairs of F rows
+  int d_row;        // weight row (w, w/r_A, w/r_B or w/r_C)
+  int n_chunks;     // point range split into n_chunks partial sums
+  int64_t res_off;  // m x n FP64 result
+  int64_t part_off; // n_chunks x m x n FP64 partial sums
+};
+
+struct GemmItem { int block, tm, tn, chunk; };
+
+// Assembly sources (Section 4: each element from exactly one grid, V_ne summed over nuclei).
+struct SrcEntry { int64_t off; int ld, row0, col0; double z; };
+struct J3Src { int64_t off; int npairs, nW, packed, pad; };
+
+struct PointBlock { int grid; int pad; int64_t p0; };  // evaluation: 256 points of one grid
+
+}  // namespace psq
+
+// Launchers (psq_kernels.cu).  Each returns the cudaError_t of its launch.
+namespace psq {
+struct LaunchTables {
+  const DevGrid* grids;
+  const double* edges;
+  const DevShell* bshell;
+  const DevShell* ashell;
+  const double* atom_xyz;     // 3 * n_atoms
+  const PointBlock* pblocks;
+  int n_pblocks;
+  const GemmBlock* gblocks;
+  int n_gblocks;
+  const GemmItem* items;
+  int n_items;
+  const short2* pairs;
+  const int64_t* elem_begin;  // prefix sums of m*n over blocks (n_gblocks + 1)
+  int64_t n_elems;
+};
+void upload_gl_tables(const double* x, const double* w, const double* klm);  // host constants
+cudaError_t launch_eval_fp64(const LaunchTables& t, double* ops, int kinds, cudaStream_t s);
+cudaError_t launch_contract_fp64(const LaunchTables& t, const double* ops, double* part, cudaStream_t s);
+cudaError_t launch_reduce(const LaunchTables& t, const double* part, double* res, cudaStream_t s);
+cudaError_t launch_assemble(int cls, int n_atoms, int nfn, int naux, const int* fn_atom,
+                            const int* fn_local, const int* aux_atom, const int* aux_local,
+                            const SrcEntry* src, const int* src_ptr, const J3Src* j3,
+                            const double* res, double* out, cudaStream_t s);
+cudaError_t launch_grid_points(const LaunchTables& t, int g, double* out, cudaStream_t s);
+cudaError_t launch_eval_one(const LaunchTables& t, int g, int kind, double* out, int64_t ld,
+                            cudaStream_t s);
+}  // namespace psq
