@@ -122,6 +122,10 @@ psq_status psq_job_io_bytes(const psq_job* job, unsigned mask, size_t* h2d, size
 psq_status psq_profile_enable(psq_job* job, int on);
 psq_status psq_profile_read(psq_job* job, double ms[8], int counts[8]);
 
+/* Waits for `stream` and reports whether a kernel of the last psq_compute on this workspace
+ * gave up a bounded wait (PSQ_ERR_TIMEOUT); psq_compute_host calls it itself. */
+psq_status psq_check(psq_job* job, unsigned mask, void* d_workspace, void* stream);
+
 /* Diagnostics for step-by-step parity tests. */
 /* Grid g of the PSQ_ALL plan (0 <= g < n_grids; pair grids (A<B) first, then the refined
  * grids (A<B; C)): its atoms (C = -1 for an unrefined pair grid) and point count. */

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("psq_job_io_bytes", _I, [_VP, _U, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ)]),
     ("psq_profile_enable", _I, [_VP, _I]),
     ("psq_profile_read", _I, [_VP, _PD, ctypes.POINTER(_I)]),
+    ("psq_check", _I, [_VP, _U, _VP, _VP]),
     ("psq_last_error", ctypes.c_char_p, []),
 ]
 
@@ -208,6 +209,10 @@ class Job:
         _check(lib().psq_compute_host(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), ws.numel(), d, h,
                                       _stream_ptr(stream)))
         return host_out
+
+    def check(self, mask, ws, stream=None):
+        """Waits for the stream; raises PsqError(PSQ_ERR_TIMEOUT) if a kernel gave up a wait."""
+        _check(lib().psq_check(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
 
     def io_bytes(self, mask=ALL):
         h, d = ctypes.c_size_t(), ctypes.c_size_t()

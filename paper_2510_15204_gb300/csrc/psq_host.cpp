@@ -129,7 +129,14 @@ struct Plan {
   // workspace layout (bytes)
   size_t table_bytes = 0, ops_off = 0, part_off = 0, res_off = 0, ws_bytes = 0;
   size_t o_grids, o_edges, o_bsh, o_ash, o_xyz, o_pb, o_gb, o_it, o_pairs, o_eb;
-  size_t o_fa, o_fl, o_aa, o_al, o_src[4], o_ptr[4], o_j3;
+  size_t o_fa, o_fl, o_aa, o_al, o_src[4], o_ptr[4], o_j3, o_status;
+  // mixed path
+  bool mixed = false;
+  std::vector<MmaBlock> mblocks;
+  std::vector<GemmItem> mitems;
+  size_t o_mb = 0, o_mi = 0, nodes_off = 0;
+  int64_t n_nodes = 0;
+  int max_node_entries = 0;
   double* staging = nullptr;  // copy of the tables, page-locked when pinned
   bool pinned = false;
   int64_t n_points = 0;
@@ -285,7 +292,12 @@ psq_status build_grid(const psq_job* j, GridKey key, DevGrid& g, std::vector<dou
       g.t_phi_all = on_axis ? 1 : 0;
       const int nph = on_axis ? sp.n_phi : (sp.n_phi == 1 ? 1 : 2);
       g.n_touch = (g.t_mu1 - g.t_mu0 + 1) * (g.t_nu1 - g.t_nu0 + 1) * nph;
+      g.nt_mu = g.t_mu1 - g.t_mu0 + 1;
+      g.nt_nu = g.t_nu1 - g.t_nu0 + 1;
+      g.nt_phi = nph;
     }
+    g.xc = xc;
+    g.zc = zc;
   }
   g.edge_off = (int)edges.size();
   edges.insert(edges.end(), mu.begin(), mu.end());
@@ -320,7 +332,9 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     if (st != PSQ_OK) return st;
   }
   // operand rows and shells per grid
-  int64_t ops = 0;  // doubles
+  P.mixed = j->prec == PSQ_MIXED;
+  const size_t esize = P.mixed ? sizeof(float) : sizeof(double);
+  int64_t ops = 0;  // elements
   for (auto& g : P.grids) {
     const bool refined = g.C >= 0;
     g.nFA = j->nb[g.A];
@@ -351,7 +365,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     }
     g.row_W = rows;
     rows += 4;
-    g.ld = (int64_t)align_up((size_t)g.K, 32);
+    g.ld = (int64_t)align_up((size_t)g.K, 64);
     g.op_off = ops;
     ops += (int64_t)rows * g.ld;
     P.n_points += g.K;
@@ -441,6 +455,50 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       for (int x = 0; x < tm; ++x)
         for (int y = 0; y < tn; ++y) P.items.push_back(GemmItem{(int)bi, x, y, c});
   }
+  if (P.mixed) {
+    // tensor-core blocks: the bigger / product side as the 128-row A operand
+    P.items.clear();
+    int64_t mtiles = 0;
+    for (auto& b : P.gblocks) {
+      MmaBlock mb{};
+      mb.grid = b.grid;
+      mb.res_off = b.res_off;
+      if (b.b_mode == 1) {
+        mb.m = b.n; mb.n = b.m; mb.a_mode = 1; mb.a_row = b.b_row; mb.a_w = -1; mb.pair_off = b.pair_off;
+        mb.b_row = b.a_row; mb.b_w = b.d_row; mb.transpose_out = 1;
+      } else {
+        mb.m = b.m; mb.n = b.n; mb.a_mode = 0; mb.a_row = b.a_row; mb.a_w = -1; mb.pair_off = 0;
+        mb.b_row = b.b_row; mb.b_w = b.d_row; mb.transpose_out = 0;
+      }
+      mtiles += (int64_t)((mb.m + 127) / 128) * ((mb.n + 63) / 64);
+      P.mblocks.push_back(mb);
+    }
+    const int64_t want = 2LL * kSmCount * 3;
+    const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
+    part = 0;
+    for (size_t bi = 0; bi < P.mblocks.size(); ++bi) {
+      MmaBlock& mb = P.mblocks[bi];
+      GemmBlock& gb = P.gblocks[bi];
+      const int64_t nch = (P.grids[mb.grid].K + 63) / 64;
+      mb.n_ranges = (int)std::max<int64_t>(1, std::min<int64_t>(cr, (nch + 15) / 16));
+      mb.part_off = part;
+      gb.n_chunks = mb.n_ranges;
+      gb.part_off = part;
+      part += (int64_t)mb.n_ranges * mb.m * mb.n;
+      const int tm = (mb.m + 127) / 128, tn = (mb.n + 63) / 64;
+      for (int c = 0; c < mb.n_ranges; ++c)
+        for (int x = 0; x < tm; ++x)
+          for (int y = 0; y < tn; ++y) P.mitems.push_back(GemmItem{(int)bi, x, y, c});
+    }
+    // node tables
+    for (auto& g : P.grids) {
+      g.nt_off = (int)P.n_nodes;
+      const int n = (g.n_mu + g.nt_mu * g.n_sp) * g.q_mu + (g.n_nu + g.nt_nu * g.n_sp) * g.q_nu +
+                    (g.n_phi + g.nt_phi * g.n_sp) * g.q_phi;
+      P.n_nodes += n;
+      P.max_node_entries = std::max(P.max_node_entries, n);
+    }
+  }
   P.elem_begin.resize(P.gblocks.size() + 1);
   P.elem_begin[0] = 0;
   for (size_t bi = 0; bi < P.gblocks.size(); ++bi)
@@ -509,7 +567,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   }
   int nclasses = 0;
   for (int c = 0; c < 5; ++c) nclasses += (mask >> c) & 1;
-  P.launches = P.grids.empty() ? 0 : 3 + nclasses;
+  P.launches = P.grids.empty() ? 0 : (P.mixed ? 4 : 3) + nclasses;
   // table layout
   size_t off = 0;
   auto sec = [&](size_t bytes) {
@@ -536,9 +594,14 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     P.o_ptr[c] = sec(sizeof(int) * P.src_ptr[c].size());
   }
   P.o_j3 = sec(sizeof(J3Src) * P.j3.size());
+  P.o_mb = sec(sizeof(MmaBlock) * P.mblocks.size());
+  P.o_mi = sec(sizeof(GemmItem) * P.mitems.size());
+  P.o_status = sec(sizeof(int) * 4);
   P.table_bytes = off;
+  P.nodes_off = off;
+  off = align_up(off + sizeof(NodeEntry) * (size_t)P.n_nodes, 256);
   P.ops_off = off;
-  off = align_up(off + sizeof(double) * (size_t)ops, 256);
+  off = align_up(off + esize * (size_t)ops, 256);
   P.part_off = off;
   off = align_up(off + sizeof(double) * (size_t)part, 256);
   P.res_off = off;
@@ -582,6 +645,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     put(P.o_ptr[c], P.src_ptr[c].data(), sizeof(int) * P.src_ptr[c].size());
   }
   put(P.o_j3, P.j3.data(), sizeof(J3Src) * P.j3.size());
+  put(P.o_mb, P.mblocks.data(), sizeof(MmaBlock) * P.mblocks.size());
+  put(P.o_mi, P.mitems.data(), sizeof(GemmItem) * P.mitems.size());
   return PSQ_OK;
 }
 
@@ -667,6 +732,7 @@ psq_status psq_context_create(int device, psq_context** out) {
       klm[l * l + l + m] = k;
     }
   upload_gl_tables(x, w, klm);
+  upload_mixed_tables(x, w, klm);
   CUDA_TRY(cudaGetLastError());
   psq_context* c = new (std::nothrow) psq_context{device};
   if (!c) return fail(PSQ_ERR_OOM, "context allocation failed");
@@ -784,10 +850,6 @@ psq_status psq_job_create(psq_context* ctx, const psq_atom* atoms, int n_atoms, 
     }
     j->nn[X] = best;
   }
-  if (precision == PSQ_MIXED) {
-    delete j;
-    return fail(PSQ_ERR_UNSUPPORTED, "mixed precision is not built in this library");
-  }
   *out = j;
   return PSQ_OK;
 }
@@ -848,13 +910,24 @@ psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws
   CUDA_TRY(mark(job, 0, s));
   CUDA_TRY(cudaMemcpyAsync(ws, P->staging, P->table_bytes, cudaMemcpyHostToDevice, s));
   const LaunchTables t = tables_at(*P, ws);
-  double* ops = (double*)(ws + P->ops_off);
   double* part = (double*)(ws + P->part_off);
   double* res = (double*)(ws + P->res_off);
-  CUDA_TRY(mark(job, 1, s));
-  CUDA_TRY(launch_eval_fp64(t, ops, 0, s));
-  CUDA_TRY(mark(job, 2, s));
-  CUDA_TRY(launch_contract_fp64(t, ops, part, s));
+  if (P->mixed) {
+    float* ops = (float*)(ws + P->ops_off);
+    NodeEntry* nodes = (NodeEntry*)(ws + P->nodes_off);
+    CUDA_TRY(mark(job, 1, s));
+    CUDA_TRY(launch_nodes(t.grids, (int)P->grids.size(), P->max_node_entries, t.edges, nodes, s));
+    CUDA_TRY(launch_eval_mixed(t, nodes, ops, s));
+    CUDA_TRY(mark(job, 2, s));
+    CUDA_TRY(launch_contract_mma(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
+                                 (int)P->mitems.size(), t.pairs, ops, part, (int*)(ws + P->o_status), s));
+  } else {
+    double* ops = (double*)(ws + P->ops_off);
+    CUDA_TRY(mark(job, 1, s));
+    CUDA_TRY(launch_eval_fp64(t, ops, 0, s));
+    CUDA_TRY(mark(job, 2, s));
+    CUDA_TRY(launch_contract_fp64(t, ops, part, s));
+  }
   CUDA_TRY(mark(job, 3, s));
   CUDA_TRY(launch_reduce(t, part, res, s));
   CUDA_TRY(mark(job, 4, s));
@@ -936,6 +1009,19 @@ psq_status psq_compute_host(psq_job* job, unsigned mask, void* d_workspace, size
     CUDA_TRY(cudaMemcpyAsync(h_out[c], d_out[c], n * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   CUDA_TRY(cudaStreamSynchronize(s));
+  return psq_check(job, mask, d_workspace, stream);
+}
+
+psq_status psq_check(psq_job* job, unsigned mask, void* d_workspace, void* stream) {
+  if (!job || !d_workspace) return fail(PSQ_ERR_ARG, "NULL argument");
+  Plan* P = nullptr;
+  psq_status st = get_plan(job, mask, &P);
+  if (st != PSQ_OK) return st;
+  int flag = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(&flag, (char*)d_workspace + P->o_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (flag) return fail(PSQ_ERR_TIMEOUT, "a bounded device wait expired (status word %d)", flag);
   return PSQ_OK;
 }
 

@@ -39,6 +39,28 @@ struct DevGrid {
   int shb_A0, shb_A1, shb_B0, shb_B1;     // basis shell ranges of A and B
   int sha_0, sha_1, sha_2, sha_3;         // aux shells: [0,1) first centre, [2,3) second
   int aux_c0, aux_c1;                     // atoms of the two aux ranges (-1 none)
+  // mixed path: 1-D node tables (rows: the N volume-element rows, then N_SP sub-rows of each
+  // touching row), and the third centre's pair-frame coordinates (xc, 0, zc)
+  int nt_off, nt_mu, nt_nu, nt_phi;
+  double xc, zc;
+};
+
+// One Gauss-Legendre node of one dimension of one grid row (FP64): the coordinate v, its
+// sine/cosine (sinh/cosh for mu), sin^2(v/2) (sinh^2 for mu), cos^2(v/2), and the 1-D weight.
+struct NodeEntry { double v, s, c, h2, g2, w; };
+
+// A contraction block of the tensor-core path: out = sum_p A_r(p) B_c(p) with
+// A_r = src[a_row + r] (* src[a_w]) or, a_mode 1, src[a_row + i] * src[a_row + j] for pair r,
+// and B_c = src[b_row + c] (* src[b_w]).  transpose_out stores the m x n result as [c][r].
+struct MmaBlock {
+  int grid;
+  int m, n;
+  int a_mode, a_row, a_w, pair_off;
+  int b_row, b_w;
+  int transpose_out;
+  int n_ranges;
+  int pad;
+  int64_t res_off, part_off;
 };
 
 // One output block of a contraction (eq 9): out[r][c] = sum_p A_r(p) d(p) B_c(p), where
@@ -93,6 +115,11 @@ cudaError_t launch_assemble(int cls, int n_atoms, int nfn, int naux, const int* 
                             const SrcEntry* src, const int* src_ptr, const J3Src* j3,
                             const double* res, double* out, cudaStream_t s);
 cudaError_t launch_grid_points(const LaunchTables& t, int g, double* out, cudaStream_t s);
-cudaError_t launch_eval_one(const LaunchTables& t, int g, int kind, double* out, int64_t ld,
-                            cudaStream_t s);
+void upload_mixed_tables(const double* x, const double* w, const double* klm);
+cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, const double* edges, NodeEntry* tab,
+                         cudaStream_t s);
+cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, float* ops, cudaStream_t s);
+cudaError_t launch_contract_mma(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
+                                const short2* pairs, const float* ops, double* part, int* status, cudaStream_t s);
+size_t mma_smem_bytes();
 }  // namespace psq

@@ -94,7 +94,9 @@ def test_grid_points_collinear_and_outside(P, ctx):
         live = pts[3] != 0.0
         ref = oracle.build_grid(job.atoms, job.spec_for_pair(A, B), A, B, C)
         assert live.sum() == len(ref["w"]), (A, B, C)
-        np.testing.assert_allclose(pts[3, live], ref["w"], rtol=1e-13, atol=0)
+        # a 300-bohr pair next to a 1.5-bohr one: the frame and third-centre coordinates carry
+        # cancellation of order 300/1.5 ulps, and the split cells beside a moved line are thin
+        np.testing.assert_allclose(pts[3, live], ref["w"], rtol=5e-12, atol=0)
         np.testing.assert_allclose(pts[0:3, live].T, ref["P"], rtol=0, atol=1e-12 * np.abs(ref["P"]).max())
 
 
@@ -113,16 +115,18 @@ def test_function_values_match_oracle(P, ctx, kind):
         vals, pts = vals.cpu().numpy(), pts.cpu().numpy()
         live = pts[3] != 0.0
         ref = oracle.build_grid(job.atoms, job.spec_for_pair(A, B), A, B, C)
-        rows = []
+        rows, shells = [], []
         if kind in (0, 1):
             for X, key in ((A, "A"), (B, "B")):
                 sh = [s for s in job.basis if s[0] == X]
+                shells += sh
                 F, L = oracle.sto_values(sh, ref["r" + key], ref["d" + key], with_laplacian=True)
                 rows.append(F if kind == 0 else L)
         else:
             centres = [A, B] if C is None else [C]
             for X in centres:
                 sh = [s for s in job.aux if s[0] == X]
+                shells += sh
                 if X == A:
                     r, d = ref["rA"], ref["dA"]
                 elif X == B:
@@ -134,9 +138,16 @@ def test_function_values_match_oracle(P, ctx, kind):
         R = np.concatenate(rows)
         got = vals[:, live]
         assert got.shape == R.shape
-        scale = np.abs(R).max(axis=1, keepdims=True)
-        err = np.abs(got - R) / (np.abs(R) + 1e-14 * scale)
-        assert err.max() < 1e-11, (g, kind, err.max())
+        # scale of each value: the largest |value| over m of its shell at that point
+        # (harmonics have nodal planes; their direction error is relative to the shell)
+        scale = np.empty_like(R)
+        r0 = 0
+        for sh in shells:
+            nf = 2 * sh[2] + 1
+            scale[r0:r0 + nf] = np.abs(R[r0:r0 + nf]).max(axis=0)[None, :]
+            r0 += nf
+        err = np.abs(got - R) / np.maximum(scale, 1e-290)
+        assert err.max() < 1e-12, (g, kind, err.max())
 
 
 # ------------------------------------------------------------------ full path parity (a1-a9)
