@@ -122,6 +122,22 @@ psq_status psq_job_io_bytes(const psq_job* job, unsigned mask, size_t* h2d, size
 psq_status psq_profile_enable(psq_job* job, int on);
 psq_status psq_profile_read(psq_job* job, double ms[8], int counts[8]);
 
+/* Allocation-free compute (no counterpart in the paper; a service of this library).
+ * Some callers cannot allocate device memory: a host application whose own memory manager
+ * owns the GPU's memory and forbids direct cudaMalloc, or a latency-critical loop that must
+ * not pay cudaMalloc's device-wide synchronisation.  psq_compute_noalloc runs psq_compute on
+ * a scratch array of PSQ_NOALLOC_SCRATCH_BYTES compiled into the library (held by every
+ * device that loads it until exit) and allocates nothing: no cudaMalloc or cudaFree, no host
+ * allocation, no planning.  The caller still passes the job and the device outputs, and must
+ * have planned mask on this job before (psq_job_workspace(job, mask, ...)); otherwise
+ * PSQ_ERR_ARG.  A job whose workspace for mask exceeds PSQ_NOALLOC_SCRATCH_BYTES fails with
+ * PSQ_ERR_OOM.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Every call, on every stream, shares the one array and leaves its contents for the
+ * next: calls whose work overlaps on the GPU race and give undefined results. */
+#define PSQ_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+psq_status psq_compute_noalloc(psq_job* job, unsigned mask, double* d_out[5], void* stream);
+
 /* Waits for `stream` and reports whether a kernel of the last psq_compute on this workspace
  * gave up a bounded wait (PSQ_ERR_TIMEOUT); psq_compute_host calls it itself. */
 psq_status psq_check(psq_job* job, unsigned mask, void* d_workspace, void* stream);

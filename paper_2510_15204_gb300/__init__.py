@@ -65,6 +65,7 @@ SIGNATURES = [
     ("psq_profile_enable", _I, [_VP, _I]),
     ("psq_profile_read", _I, [_VP, _PD, ctypes.POINTER(_I)]),
     ("psq_check", _I, [_VP, _U, _VP, _VP]),
+    ("psq_compute_noalloc", _I, [_VP, _U, ctypes.POINTER(_VP), _VP]),
     ("psq_last_error", ctypes.c_char_p, []),
 ]
 
@@ -197,6 +198,15 @@ class Job:
             ptrs[i] = out[k].data_ptr() if k in out else None
         _check(lib().psq_compute(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), ws.numel(), ptrs,
                                  _stream_ptr(stream)))
+        return out
+
+    def compute_noalloc(self, mask, out, stream=None):
+        """psq_compute_noalloc: the library's fixed device scratch instead of a workspace;
+        mask must have been planned (workspace_bytes(mask)) first."""
+        ptrs = (ctypes.c_void_p * 5)()
+        for i, k in enumerate(CLASSES):
+            ptrs[i] = out[k].data_ptr() if k in out else None
+        _check(lib().psq_compute_noalloc(self.handle, mask, ptrs, _stream_ptr(stream)))
         return out
 
     def compute_host(self, mask, ws, out, host_out, stream=None):

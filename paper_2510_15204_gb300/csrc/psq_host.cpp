@@ -892,6 +892,15 @@ psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_
 
 psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
                        void* stream) {
+  return psq::compute_on(job, mask, d_workspace, ws_bytes, d_out, stream, false);
+}
+
+}  // extern "C"
+
+psq_status psq::set_error(psq_status s, const char* msg) { return fail(s, "%s", msg); }
+
+psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
+                           void* stream, bool plan_must_exist) {
   if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
   if (job->ctx->device < 0) return fail(PSQ_ERR_ARG, "the job's context has no device (planning only)");
   if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
@@ -900,8 +909,16 @@ psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws
   for (int c = 0; c < 5; ++c)
     if ((mask >> c) & 1 && !d_out[c]) return fail(PSQ_ERR_ARG, "output %d is NULL", c);
   Plan* P = nullptr;
-  psq_status st = get_plan(job, mask, &P);
-  if (st != PSQ_OK) return st;
+  if (plan_must_exist) {
+    std::lock_guard<std::mutex> lk(job->mu);
+    auto it = job->plans.find(mask);
+    if (it == job->plans.end())
+      return fail(PSQ_ERR_ARG, "no plan for mask 0x%x yet: call psq_job_workspace(job, mask) first", mask);
+    P = it->second.get();
+  } else {
+    psq_status st = get_plan(job, mask, &P);
+    if (st != PSQ_OK) return st;
+  }
   if (!d_workspace || ws_bytes < P->ws_bytes)
     return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->ws_bytes);
   if ((uintptr_t)d_workspace % 256) return fail(PSQ_ERR_ARG, "workspace must be 256-byte aligned");
@@ -951,6 +968,8 @@ psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws
   CUDA_TRY(mark(job, -1, s));
   return PSQ_OK;
 }
+
+extern "C" {
 
 psq_status psq_profile_enable(psq_job* job, int on) {
   if (!job) return fail(PSQ_ERR_ARG, "job is NULL");

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/psq.h"
+
 namespace psq {
 
 constexpr int kMaxL = 6;    // highest angular momentum of a basis or aux shell
@@ -122,4 +124,10 @@ cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, float
 cudaError_t launch_contract_mma(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
                                 const short2* pairs, const float* ops, double* part, int* status, cudaStream_t s);
 size_t mma_smem_bytes();
+
+// Host side (psq_host.cpp): psq_compute on a given workspace; with plan_must_exist the call
+// plans nothing (no host or device allocation) and fails if mask was never planned.
+psq_status compute_on(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
+                      void* stream, bool plan_must_exist);
+psq_status set_error(psq_status s, const char* msg);
 }  // namespace psq
