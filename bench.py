@@ -160,19 +160,20 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------ traffic record
 
-def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` from profiles/traffic.json, if recorded for the
-    current kernel source (null once the source changed since the counters were taken)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def recorded_traffic(kernel, workload, precision):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.txt, if recorded for the current
+    kernel source (null once the source changed since the counters were taken)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    try:
-        rec = json.load(open(path))[kernel][workload]
-    except Exception:
-        return None
-    src = os.path.join(ROOT, "paper_2510_15204_gb300", "csrc", rec["source"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec["bytes_per_launch"] if h == rec["sha"] else None
+    for line in open(path):
+        f = line.split("#")[0].split()
+        if len(f) != 6 or f[0] != kernel or f[1] != workload or f[2] != precision:
+            continue
+        src = os.path.join(ROOT, "paper_2510_15204_gb300", "csrc", f[3])
+        if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == f[4]:
+            return int(f[5])
+    return None
 
 
 # ------------------------------------------------------------------------------ GPU arm
@@ -260,7 +261,7 @@ def main():
         roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
     roof["kernel"] = kind
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
-    roof["traffic"] = recorded_traffic(kind, args.workload)
+    roof["traffic"] = recorded_traffic(kind, args.workload, args.precision)
     roof["share"] = kms / sum(v[0] for v in prof.values())
 
     line = {

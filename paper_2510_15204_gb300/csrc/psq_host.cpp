@@ -134,7 +134,9 @@ struct Plan {
   bool mixed = false;
   std::vector<MmaBlock> mblocks;
   std::vector<GemmItem> mitems;
-  size_t o_mb = 0, o_mi = 0, nodes_off = 0;
+  size_t o_mb = 0, o_mi = 0, nodes_off = 0, o_xi = 0, o_rc = 0;
+  std::vector<float2> xi;    // per grid: (hi, lo) scale turning rho into x = zeta r, per shell
+  std::vector<double> rowc;  // per grid: FP64 constant of every operand row
   int64_t n_nodes = 0;
   int max_node_entries = 0;
   double* staging = nullptr;  // copy of the tables, page-locked when pinned
@@ -490,6 +492,66 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
         for (int x = 0; x < tm; ++x)
           for (int y = 0; y < tn; ++y) P.mitems.push_back(GemmItem{(int)bi, x, y, c});
     }
+    // FP32-pair rotation, x-scales of the shells and FP64 row constants
+    auto klm = [](int l, int m) {
+      const int am = std::abs(m);
+      double k = std::sqrt((2 * l + 1) / (4 * M_PI) * factorial(l - am) / factorial(l + am));
+      return m != 0 ? k * std::sqrt(2.0) : k;
+    };
+    auto split = [](double v) {
+      const float hi = (float)v;
+      return make_float2(hi, (float)(v - (double)hi));
+    };
+    for (auto& g : P.grids) {
+      for (int i = 0; i < 9; ++i) {
+        g.Rh[i] = (float)g.R[i];
+        g.Rl[i] = (float)(g.R[i] - (double)g.Rh[i]);
+      }
+      g.xi_off = (int)P.xi.size();
+      auto add_xi = [&](const std::vector<DevShell>& sh, int s0, int s1, bool focus) {
+        for (int q = s0; q < s1; ++q) P.xi.push_back(split(focus ? 2.0 * g.a * sh[q].zeta : sh[q].zeta));
+      };
+      add_xi(j->dbs, g.shb_A0, g.shb_A1, true);
+      add_xi(j->dbs, g.shb_B0, g.shb_B1, true);
+      if (g.aux_c0 >= 0) add_xi(j->das, g.sha_0, g.sha_1, g.aux_c0 == g.A || g.aux_c0 == g.B);
+      if (g.aux_c1 >= 0) add_xi(j->das, g.sha_2, g.sha_3, g.aux_c1 == g.A || g.aux_c1 == g.B);
+      g.rc_off = (int)P.rowc.size();
+      int nrows = g.row_W + 4;
+      P.rowc.resize(P.rowc.size() + nrows, 1.0);
+      double* rc = P.rowc.data() + g.rc_off;
+      auto basis_rows = [&](int row0, double zpow_extra) {
+        int r = row0;
+        for (int c = 0; c < 2; ++c) {
+          const int s0 = c == 0 ? g.shb_A0 : g.shb_B0, s1 = c == 0 ? g.shb_A1 : g.shb_B1;
+          for (int q = s0; q < s1; ++q) {
+            const DevShell& d = j->dbs[q];
+            for (int m = -d.l; m <= d.l; ++m)
+              rc[r++] = d.norm * klm(d.l, m) * std::pow(d.zeta, -(d.n - 1) + zpow_extra);
+          }
+        }
+      };
+      if (g.row_F >= 0) basis_rows(g.row_F, 0.0);
+      if (g.row_L >= 0) basis_rows(g.row_L, 2.0);
+      auto aux_rows = [&](int row0, bool pot) {
+        int r = row0;
+        for (int c = 0; c < 2; ++c) {
+          const int s0 = c == 0 ? g.sha_0 : g.sha_2, s1 = c == 0 ? g.sha_1 : g.sha_3;
+          if ((c == 0 ? g.aux_c0 : g.aux_c1) < 0) continue;
+          for (int q = s0; q < s1; ++q) {
+            const DevShell& d = j->das[q];
+            for (int m = -d.l; m <= d.l; ++m)
+              rc[r++] = pot ? 4.0 * M_PI / (2 * d.l + 1) * d.norm * klm(d.l, m) * std::pow(d.zeta, -(d.n + 1))
+                            : d.norm * klm(d.l, m) * std::pow(d.zeta, -(d.n - 1));
+          }
+        }
+      };
+      if (g.row_G >= 0) aux_rows(g.row_G, false);
+      if (g.row_U >= 0) aux_rows(g.row_U, true);
+      rc[g.row_W + 0] = g.a * g.a * g.a;
+      rc[g.row_W + 1] = 0.5 * g.a * g.a;
+      rc[g.row_W + 2] = 0.5 * g.a * g.a;
+      rc[g.row_W + 3] = g.a * g.a * g.a;
+    }
     // node tables
     for (auto& g : P.grids) {
       g.nt_off = (int)P.n_nodes;
@@ -597,6 +659,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   P.o_mb = sec(sizeof(MmaBlock) * P.mblocks.size());
   P.o_mi = sec(sizeof(GemmItem) * P.mitems.size());
   P.o_status = sec(sizeof(int) * 4);
+  P.o_xi = sec(sizeof(float2) * P.xi.size());
+  P.o_rc = sec(sizeof(double) * P.rowc.size());
   P.table_bytes = off;
   P.nodes_off = off;
   off = align_up(off + sizeof(NodeEntry) * (size_t)P.n_nodes, 256);
@@ -647,6 +711,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   put(P.o_j3, P.j3.data(), sizeof(J3Src) * P.j3.size());
   put(P.o_mb, P.mblocks.data(), sizeof(MmaBlock) * P.mblocks.size());
   put(P.o_mi, P.mitems.data(), sizeof(GemmItem) * P.mitems.size());
+  put(P.o_xi, P.xi.data(), sizeof(float2) * P.xi.size());
+  put(P.o_rc, P.rowc.data(), sizeof(double) * P.rowc.size());
   return PSQ_OK;
 }
 
@@ -934,10 +1000,11 @@ psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_
     NodeEntry* nodes = (NodeEntry*)(ws + P->nodes_off);
     CUDA_TRY(mark(job, 1, s));
     CUDA_TRY(launch_nodes(t.grids, (int)P->grids.size(), P->max_node_entries, t.edges, nodes, s));
-    CUDA_TRY(launch_eval_mixed(t, nodes, ops, s));
+    CUDA_TRY(launch_eval_mixed(t, nodes, (const float2*)(ws + P->o_xi), ops, s));
     CUDA_TRY(mark(job, 2, s));
     CUDA_TRY(launch_contract_mma(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
-                                 (int)P->mitems.size(), t.pairs, ops, part, (int*)(ws + P->o_status), s));
+                                 (int)P->mitems.size(), t.pairs, ops, (const double*)(ws + P->o_rc), part,
+                                 (int*)(ws + P->o_status), s));
   } else {
     double* ops = (double*)(ws + P->ops_off);
     CUDA_TRY(mark(job, 1, s));

@@ -45,6 +45,9 @@ struct DevGrid {
   // touching row), and the third centre's pair-frame coordinates (xc, 0, zc)
   int nt_off, nt_mu, nt_nu, nt_phi;
   double xc, zc;
+  float Rh[9], Rl[9];  // R as an FP32 pair
+  int xi_off;          // FP32 (hi, lo) x-scales of the shells: basis A, basis B, aux c0, aux c1
+  int rc_off;          // FP64 constant of every operand row (norms, zeta powers, a^3 ...)
 };
 
 // One Gauss-Legendre node of one dimension of one grid row (FP64): the coordinate v, its
@@ -120,9 +123,11 @@ cudaError_t launch_grid_points(const LaunchTables& t, int g, double* out, cudaSt
 void upload_mixed_tables(const double* x, const double* w, const double* klm);
 cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, const double* edges, NodeEntry* tab,
                          cudaStream_t s);
-cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, float* ops, cudaStream_t s);
+cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const float2* xi, float* ops,
+                              cudaStream_t s);
 cudaError_t launch_contract_mma(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                                const short2* pairs, const float* ops, double* part, int* status, cudaStream_t s);
+                                const short2* pairs, const float* ops, const double* rowc, double* part,
+                                int* status, cudaStream_t s);
 size_t mma_smem_bytes();
 
 // Host side (psq_host.cpp): psq_compute on a given workspace; with plan_must_exist the call

