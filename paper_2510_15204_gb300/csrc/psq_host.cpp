@@ -108,6 +108,7 @@ Vec3 cross(Vec3 a, Vec3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.
 
 struct psq_context {
   int device;
+  int sm_count = 152;
 };
 
 namespace {
@@ -475,7 +476,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       mtiles += (int64_t)((mb.m + 127) / 128) * ((mb.n + 63) / 64);
       P.mblocks.push_back(mb);
     }
-    const int64_t want = 2LL * kSmCount * 3;
+    const int64_t want = 4LL * kSmCount;
     const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
     part = 0;
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi) {
@@ -492,6 +493,15 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
         for (int x = 0; x < tm; ++x)
           for (int y = 0; y < tn; ++y) P.mitems.push_back(GemmItem{(int)bi, x, y, c});
     }
+    // longest items first: the persistent CTAs take them round-robin
+    auto item_chunks = [&](const GemmItem& it) {
+      const MmaBlock& mb = P.mblocks[it.block];
+      const int64_t nch = (P.grids[mb.grid].K + 63) / 64;
+      const int64_t per = (nch + mb.n_ranges - 1) / mb.n_ranges;
+      return std::max<int64_t>(0, std::min<int64_t>(nch, per * (it.chunk + 1)) - per * it.chunk);
+    };
+    std::stable_sort(P.mitems.begin(), P.mitems.end(),
+                     [&](const GemmItem& x, const GemmItem& y) { return item_chunks(x) > item_chunks(y); });
     // FP32-pair rotation, x-scales of the shells and FP64 row constants
     auto klm = [](int l, int m) {
       const int am = std::abs(m);
@@ -800,7 +810,9 @@ psq_status psq_context_create(int device, psq_context** out) {
   upload_gl_tables(x, w, klm);
   upload_mixed_tables(x, w, klm);
   CUDA_TRY(cudaGetLastError());
-  psq_context* c = new (std::nothrow) psq_context{device};
+  int sms = 0;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  psq_context* c = new (std::nothrow) psq_context{device, sms > 0 ? sms : 152};
   if (!c) return fail(PSQ_ERR_OOM, "context allocation failed");
   *out = c;
   return PSQ_OK;
@@ -1002,18 +1014,22 @@ psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_
     CUDA_TRY(launch_nodes(t.grids, (int)P->grids.size(), P->max_node_entries, t.edges, nodes, s));
     CUDA_TRY(launch_eval_mixed(t, nodes, (const float2*)(ws + P->o_xi), ops, s));
     CUDA_TRY(mark(job, 2, s));
-    CUDA_TRY(launch_contract_mma(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
-                                 (int)P->mitems.size(), t.pairs, ops, (const double*)(ws + P->o_rc), part,
-                                 (int*)(ws + P->o_status), s));
+    const int n_items = (int)P->mitems.size();
+    CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi), n_items,
+                                std::min(n_items, job->ctx->sm_count), t.pairs, ops, (float2*)part,
+                                (int*)(ws + P->o_status), s));
+    CUDA_TRY(mark(job, 3, s));
+    CUDA_TRY(launch_reduce_mixed(t.grids, (const MmaBlock*)(ws + P->o_mb), (int)P->mblocks.size(), t.elem_begin,
+                                 t.n_elems, t.pairs, (const double*)(ws + P->o_rc), (const float2*)part, res, s));
   } else {
     double* ops = (double*)(ws + P->ops_off);
     CUDA_TRY(mark(job, 1, s));
     CUDA_TRY(launch_eval_fp64(t, ops, 0, s));
     CUDA_TRY(mark(job, 2, s));
     CUDA_TRY(launch_contract_fp64(t, ops, part, s));
+    CUDA_TRY(mark(job, 3, s));
+    CUDA_TRY(launch_reduce(t, part, res, s));
   }
-  CUDA_TRY(mark(job, 3, s));
-  CUDA_TRY(launch_reduce(t, part, res, s));
   CUDA_TRY(mark(job, 4, s));
   const int* fa = (const int*)(ws + P->o_fa);
   const int* fl = (const int*)(ws + P->o_fl);

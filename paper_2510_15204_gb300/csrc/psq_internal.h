@@ -125,10 +125,13 @@ cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, con
                          cudaStream_t s);
 cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const float2* xi, float* ops,
                               cudaStream_t s);
-cudaError_t launch_contract_mma(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                                const short2* pairs, const float* ops, const double* rowc, double* part,
-                                int* status, cudaStream_t s);
-size_t mma_smem_bytes();
+size_t ws_smem_bytes();
+cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
+                               int n_ctas, const short2* pairs, const float* ops, float2* part, int* status,
+                               cudaStream_t s);
+cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
+                                int64_t n_elems, const short2* pairs, const double* rowc, const float2* part,
+                                double* res, cudaStream_t s);
 
 // Host side (psq_host.cpp): psq_compute on a given workspace; with plan_must_exist the call
 // plans nothing (no host or device allocation) and fails if mask was never planned.

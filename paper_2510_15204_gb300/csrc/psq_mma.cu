@@ -8,14 +8,15 @@
 //    potentials (eq 16, incomplete gamma by its positive series below x = k) in FP32 as
 //    functions of x = zeta r (x from an FP32 hi+lo scale, first-order corrected); every
 //    constant factor of a row is left to FP64;
-//  * contract_mma_kernel: the weighted contraction of eq 9 on tcgen05 tensor cores.  Every
+//  * contract_ws_kernel: the weighted contraction of eq 9 on tcgen05 tensor cores.  Every
 //    operand row of a 64-point chunk is scaled by a power of two from its maximum and cut
 //    into four integer slices of at most 8 bits (exact in BF16).  Ten BF16 MMAs per K step
 //    accumulate the slice products by order (0..3) into four FP32 TMEM accumulators; all
 //    partial sums are integers below 2^24, so the FP32 accumulation is exact.  After each
 //    chunk the accumulators are scaled back and added into double-float (FP32 hi + lo)
-//    registers; each CTA writes its point range's sum in FP64, times the FP64 constants of
-//    its row and column (normalisations, powers of zeta, a^3), which the FP32 values omit.
+//    registers; each work item writes its point range's (hi, lo) sums, and reduce_mixed_kernel
+//    adds the ranges in FP64 and applies the FP64 constants of each row and column
+//    (normalisations, powers of zeta, a^3), which the FP32 values omit.
 #include "psq_internal.h"
 
 #include <cuda_bf16.h>
@@ -336,7 +337,6 @@ constexpr int kM = 128;         // tile rows (pairs, or the bigger side of a 2-i
 constexpr int kTileN = 64;       // tile columns
 constexpr int kChunk = 64;      // points per scale window and smem stage (128 bytes of BF16)
 constexpr int kSlices = 4;      // 8-bit integer slices per operand value (orders 0..3 kept)
-constexpr int kThreads = 128;
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -409,54 +409,90 @@ __device__ __forceinline__ float pow2f(int k) {
   return __int_as_float((k + 127) << 23);
 }
 
-// Cuts 64 values of one operand row into four integer BF16 slices in the K-major 128-byte
-// swizzled layout: v 2^(7-e) = a0 + a1/256 + a2/256^2 + a3/256^3, |a_i| <= 128, |v| < 2^e.
-// Returns e (a large negative value for an all-zero row).
-__device__ __forceinline__ int slice_row(const float* v, int row, uint8_t* const* sl) {
-  float mx = 0.0f;
-#pragma unroll
-  for (int i = 0; i < kChunk; ++i) mx = fmaxf(mx, fabsf(v[i]));
-  int e = 0;
-  if (mx > 0.0f) frexpf(mx, &e);
-  const bool zero = !(mx > 0.0f) || e < -110;
-  const float sc = zero ? 0.0f : pow2f(7 - e);
+}  // namespace mma
+
+// ------------------------------------------------------------------ warp-specialised version
+//
+// One persistent CTA per SM (512 threads).  Warps 0-7 produce: for each 64-point chunk they
+// build the A tile (128 rows) and the B tile (<= 64 rows) as four integer slices in one of two
+// shared-memory stages, two threads per row (32 points each); lane 0 of warp 0 then issues
+// the chunk's 40 MMAs into one of two TMEM accumulator sets and commits them to full[stage].
+// Warps 8-15 fold: they wait full[stage], read the four order accumulators of their lane
+// quadrant and column half, add the chunk into double-float registers and arrive at
+// free[stage], which lets the producers reuse the stage and the TMEM set.  A CTA's point
+// range ends with a write of (hi, lo) pairs; the FP64 reduction applies the row constants.
+
+namespace ws {
+
+constexpr int kProducers = 256;
+constexpr int kEpi = 256;
+constexpr int kThreads = kProducers + kEpi;
+constexpr int kStages = 2;
+
+struct Smem {
+  alignas(1024) uint8_t a[kStages][mma::kSlices][mma::kM * 128];
+  alignas(1024) uint8_t b[kStages][mma::kSlices][mma::kTileN * 128];
+  int ea[kStages][mma::kM];
+  int eb[kStages][mma::kTileN];
+  alignas(8) uint64_t full[kStages];
+  alignas(8) uint64_t freed[kStages];
+  uint32_t tmem_base;
+  int abort;
+};
+
+// Barrier of the 256 producer threads that also ORs a predicate over them, so every producer
+// takes the same decision from it.
+__device__ __forceinline__ bool named_sync_producers_or(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "n"(kProducers)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar) : "memory");
+}
+
+// 32 values of half a row -> four slices (bytes [64h, 64h+64) of the row in each slice).
+__device__ __forceinline__ void slice_half(const float* v, float sc, int row, int h, uint8_t* const* sl) {
   const uint32_t rowoff = (uint32_t)row * 128u;
   const uint32_t sw = (uint32_t)(row & 7);
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {  // 16-byte chunk c holds points 8c .. 8c+7
-    uint32_t w[kSlices][4];
+  for (int cc = 0; cc < 4; ++cc) {
+    const int c = 4 * h + cc;  // 16-byte chunk index within the 128-byte row
+    uint32_t w[mma::kSlices][4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      uint32_t b[kSlices][2];
+    for (int q = 0; q < 4; ++q) {
+      float r0 = v[8 * cc + 2 * q] * sc, r1 = v[8 * cc + 2 * q + 1] * sc;
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        float r = v[8 * c + 2 * h + u] * sc;
-#pragma unroll
-        for (int k = 0; k < kSlices; ++k) {
-          const float a = rintf(r);
-          b[k][u] = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-          r = (r - a) * 256.0f;
-        }
+      for (int k = 0; k < mma::kSlices; ++k) {
+        const float a0 = rintf(r0), a1 = rintf(r1);
+        const __nv_bfloat162 p = __floats2bfloat162_rn(a0, a1);
+        w[k][q] = *reinterpret_cast<const uint32_t*>(&p);
+        r0 = (r0 - a0) * 256.0f;
+        r1 = (r1 - a1) * 256.0f;
       }
-#pragma unroll
-      for (int k = 0; k < kSlices; ++k) w[k][h] = b[k][0] | (b[k][1] << 16);
     }
     const uint32_t off = rowoff + (((uint32_t)c ^ sw) << 4);
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k)
+    for (int k = 0; k < mma::kSlices; ++k)
       *reinterpret_cast<uint4*>(sl[k] + off) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
   }
-  return zero ? -100000 : e;
 }
 
-// v[i] = src[k0 + i] (* mul[k0 + i] when mul is given), zero past K.
-__device__ __forceinline__ void load64(const float* __restrict__ src, const float* __restrict__ mul, int64_t k0,
+__device__ __forceinline__ void load32(const float* __restrict__ src, const float* __restrict__ mul, int64_t k0,
                                        int64_t K, float* v) {
-  if (k0 + kChunk <= K) {
+  if (k0 + 32 <= K) {
     const float4* s4 = reinterpret_cast<const float4*>(src + k0);
     const float4* m4 = reinterpret_cast<const float4*>(mul + k0);
 #pragma unroll
-    for (int i = 0; i < kChunk / 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
       float4 q = __ldg(s4 + i);
       if (mul) {
         const float4 m = __ldg(m4 + i);
@@ -466,191 +502,266 @@ __device__ __forceinline__ void load64(const float* __restrict__ src, const floa
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < kChunk; ++i) v[i] = (k0 + i < K) ? src[k0 + i] * (mul ? mul[k0 + i] : 1.0f) : 0.0f;
+    for (int i = 0; i < 32; ++i) v[i] = (k0 + i < K) ? src[k0 + i] * (mul ? mul[k0 + i] : 1.0f) : 0.0f;
   }
 }
 
-struct Smem {
-  alignas(1024) uint8_t a[kSlices][kM * 128];       // A slices: 128 rows x 64 points BF16
-  alignas(1024) uint8_t b[kSlices][kTileN * 128];   // B slices: up to 64 rows
-  int ea[kM];
-  int eb[kTileN];
-  alignas(8) uint64_t mbar;
-  uint32_t tmem_base;
-};
+// One producer task: half h of operand row `row` of the tile (values from the grid's FP32
+// rows), sliced into stage `st`.  Returns nothing; the row's exponent goes to *e_out (h == 0).
+__device__ __forceinline__ void produce_half(const float* src, const float* mul, int64_t k0, int64_t K, bool valid,
+                                             int row, int h, uint8_t* const* sl, int* e_out) {
+  float v[32];
+  if (valid) {
+    load32(src, mul, k0 + 32 * h, K, v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+  }
+  float mx = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[i]));
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  int e = 0;
+  if (mx > 0.0f) frexpf(mx, &e);
+  const bool zero = !(mx > 0.0f) || e < -110;
+  slice_half(v, zero ? 0.0f : mma::pow2f(7 - e), row, h, sl);
+  if (h == 0) *e_out = zero ? -100000 : e;
+}
 
-}  // namespace mma
+}  // namespace ws
 
-__global__ void __launch_bounds__(mma::kThreads) contract_mma_kernel(const DevGrid* __restrict__ grids,
+__global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevGrid* __restrict__ grids,
                                                                       const MmaBlock* __restrict__ blocks,
-                                                                      const GemmItem* __restrict__ items,
+                                                                      const GemmItem* __restrict__ items, int n_items,
                                                                       const short2* __restrict__ pairs,
                                                                       const float* __restrict__ ops,
-                                                                      const double* __restrict__ rowc,
-                                                                      double* __restrict__ part,
+                                                                      float2* __restrict__ part,
                                                                       int* __restrict__ status) {
   using namespace mma;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const GemmItem it = items[blockIdx.x];
-  const MmaBlock b = blocks[it.block];
-  const DevGrid& g = grids[b.grid];
-  const float* base = ops + g.op_off;
-  const int64_t ld = g.ld, K = g.K;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = min(kTileN, b.n - it.tn * kTileN);           // columns in this tile
-  const int ntp = (nt + 15) & ~15;                           // MMA N (multiple of 16)
-  const int ncols = kSlices * ntp <= 32 ? 32 : (kSlices * ntp <= 64 ? 64 : (kSlices * ntp <= 128 ? 128 : 256));
-  const int r0 = it.tm * kM, c0 = it.tn * kTileN;
-  // point range of this item, in whole chunks
-  const int64_t nchunk = (K + kChunk - 1) / kChunk;
-  const int64_t per = (nchunk + b.n_ranges - 1) / b.n_ranges;
-  const int64_t ch0 = (int64_t)it.chunk * per, ch1 = min(nchunk, ch0 + per);
-
-  if (warp == 0) {
+  ws::Smem& sm = *reinterpret_cast<ws::Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
-                 "r"(ncols));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.mbar)));
+    for (int s = 0; s < ws::kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&sm.freed[s])));
+    }
+    sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm.tmem_base;
-  const uint32_t idesc = make_idesc(ntp);
+  uint32_t c = 0;  // chunks of this CTA so far (stage = c & 1, TMEM set = c & 1)
 
-  float H[kTileN], L[kTileN];
-#pragma unroll
-  for (int c = 0; c < kTileN; ++c) { H[c] = 0.0f; L[c] = 0.0f; }
-  bool ok = true;
-  uint32_t phase = 0;
-
-  const int row = r0 + tid;  // this thread's A row
-  short2 pr = make_short2(0, 0);
-  if (b.a_mode == 1 && row < b.m) pr = pairs[b.pair_off + row];
-
-  for (int64_t ch = ch0; ch < ch1 && ok; ++ch) {
-    const int64_t k0 = ch * kChunk;
-    float v[kChunk];
-    // ---- A row tid
-    if (row < b.m) {
-      if (b.a_mode == 1)
-        load64(base + (int64_t)(b.a_row + pr.x) * ld, base + (int64_t)(b.a_row + pr.y) * ld, k0, K, v);
-      else
-        load64(base + (int64_t)(b.a_row + row) * ld, b.a_w >= 0 ? base + (int64_t)b.a_w * ld : nullptr, k0, K, v);
-    } else {
-#pragma unroll
-      for (int i = 0; i < kChunk; ++i) v[i] = 0.0f;
-    }
-    {
-      uint8_t* sl[kSlices] = {sm.a[0], sm.a[1], sm.a[2], sm.a[3]};
-      sm.ea[tid] = slice_row(v, tid, sl);
-    }
-    // ---- B row tid (columns of the tile)
-    if (tid < ntp) {
-      if (tid < nt) {
-        load64(base + (int64_t)(b.b_row + c0 + tid) * ld, b.b_w >= 0 ? base + (int64_t)b.b_w * ld : nullptr, k0, K,
-               v);
-      } else {
-#pragma unroll
-        for (int i = 0; i < kChunk; ++i) v[i] = 0.0f;
-      }
-      uint8_t* sl[kSlices] = {sm.b[0], sm.b[1], sm.b[2], sm.b[3]};
-      sm.eb[tid] = slice_row(v, tid, sl);
-    }
-    fence_async_smem();
-    __syncthreads();
-    // ---- MMA issue (one thread): 4 K steps x 10 slice products into 4 accumulators by order
-    if (tid == 0) {
-      fence_after();
-#pragma unroll
-      for (int k = 0; k < kChunk / 16; ++k) {
-        const uint32_t ko = 32u * k;
-#pragma unroll
-        for (int ord = 0; ord < kSlices; ++ord) {
-#pragma unroll
-          for (int i = 0; i <= ord; ++i) {
-            const uint64_t da = make_desc(smem_u32(sm.a[i]) + ko);
-            const uint64_t db = make_desc(smem_u32(sm.b[ord - i]) + ko);
-            mma_bf16(tmem + ord * ntp, da, db, idesc, (k > 0 || i > 0) ? 1u : 0u);
-          }
+  if (tid < ws::kProducers) {
+    // ------------------------------------------------------------ producers (+ MMA issue)
+    bool stop = false;
+    for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+      const GemmItem it = items[ii];
+      const MmaBlock b = blocks[it.block];
+      const DevGrid& g = grids[b.grid];
+      const float* base = ops + g.op_off;
+      const int64_t ld = g.ld, K = g.K;
+      const int nt = min(kTileN, b.n - it.tn * kTileN), ntp = (nt + 15) & ~15;
+      const int r0 = it.tm * kM, c0 = it.tn * kTileN;
+      const int64_t nchunk = (K + kChunk - 1) / kChunk;
+      const int64_t per = (nchunk + b.n_ranges - 1) / b.n_ranges;
+      const int64_t ch0 = (int64_t)it.chunk * per, ch1 = min(nchunk, ch0 + per);
+      const uint32_t idesc = make_idesc(ntp);
+      // this thread's A task: row tid/2, half tid%2
+      const int arow = tid >> 1, ah = tid & 1;
+      const int grow = r0 + arow;
+      const bool avalid = grow < b.m;
+      const float *asrc = nullptr, *amul = nullptr;
+      if (avalid) {
+        if (b.a_mode == 1) {
+          const short2 pr = pairs[b.pair_off + grow];
+          asrc = base + (int64_t)(b.a_row + pr.x) * ld;
+          amul = base + (int64_t)(b.a_row + pr.y) * ld;
+        } else {
+          asrc = base + (int64_t)(b.a_row + grow) * ld;
+          amul = b.a_w >= 0 ? base + (int64_t)b.a_w * ld : nullptr;
         }
       }
-      mma_commit(smem_u32(&sm.mbar));
-    }
-    __syncwarp();
-    const bool done = mbar_wait(smem_u32(&sm.mbar), phase);
-    if (__syncthreads_or(!done)) {  // the same decision in every thread of the CTA
-      ok = false;
-      if (tid == 0) atomicExch(status, 1);
-      mbar_wait(smem_u32(&sm.mbar), phase);  // one more bounded wait for MMAs still in flight
-    }
-    phase ^= 1u;
-    fence_after();
-    // ---- fold the exact chunk sums into double-float accumulators
-    if (ok) {
-      const int ea = sm.ea[tid];
-      const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+      const int brow = tid >> 1;
+      const bool btask = tid < 2 * ntp, bvalid = brow < nt;
+      const float* bsrc = bvalid ? base + (int64_t)(b.b_row + c0 + brow) * ld : nullptr;
+      const float* bmul = (bvalid && b.b_w >= 0) ? base + (int64_t)b.b_w * ld : nullptr;
+      for (int64_t ch = ch0; ch < ch1; ++ch, ++c) {
+        const int st = c & 1;
+        bool ok = true;
+        if (c >= 2) ok = mbar_wait(smem_u32(&sm.freed[st]), ((c - 2) >> 1) & 1);
+        if (!ok) atomicExch(status, 2);
+        const int64_t k0 = ch * kChunk;
+        uint8_t* asl[kSlices] = {sm.a[st][0], sm.a[st][1], sm.a[st][2], sm.a[st][3]};
+        ws::produce_half(asrc, amul, k0, K, avalid, arow, ah, asl, &sm.ea[st][arow]);
+        if (btask) {
+          uint8_t* bsl[kSlices] = {sm.b[st][0], sm.b[st][1], sm.b[st][2], sm.b[st][3]};
+          ws::produce_half(bsrc, bmul, k0, K, bvalid, brow, tid & 1, bsl, &sm.eb[st][brow]);
+        }
+        fence_async_smem();
+        // one decision for all producers: stop if any of them timed out or the fold warps did
+        if (ws::named_sync_producers_or(!ok || *(volatile int*)&sm.abort)) { stop = true; break; }
+        if (tid == 0) {
+          fence_after();
+          const uint32_t tset = tmem + (uint32_t)st * 256u;
 #pragma unroll
-      for (int gq = 0; gq < kTileN / 16; ++gq) {
-        if (gq * 16 < ntp) {
-          float hi[16], lo[16], d[16];
-          tmem_ld16(lane_base + 0 * ntp + gq * 16, hi);
-          tmem_wait_ld();
-          tmem_ld16(lane_base + 1 * ntp + gq * 16, lo);
-          tmem_wait_ld();
+          for (int k = 0; k < kChunk / 16; ++k) {
+            const uint32_t ko = 32u * k;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) lo[j] *= 0.00390625f;  // 2^-8
+            for (int ord = 0; ord < kSlices; ++ord) {
 #pragma unroll
-          for (int ord = 2; ord < kSlices; ++ord) {
-            tmem_ld16(lane_base + ord * ntp + gq * 16, d);
-            tmem_wait_ld();
-            const float sc = pow2f(-8 * ord);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) lo[j] = fmaf(d[j], sc, lo[j]);
+              for (int i = 0; i <= ord; ++i) {
+                const uint64_t da = make_desc(smem_u32(sm.a[st][i]) + ko);
+                const uint64_t db = make_desc(smem_u32(sm.b[st][ord - i]) + ko);
+                mma_bf16(tset + ord * ntp, da, db, idesc, (k > 0 || i > 0) ? 1u : 0u);
+              }
+            }
           }
+          mma_commit(smem_u32(&sm.full[st]));
+        }
+      }
+      if (stop) break;
+    }
+  } else {
+    // ------------------------------------------------------------ fold (epilogue) warps
+    const int lane = tid & 31;
+    const int ew = warp - 8;             // 0..7
+    const int quad = warp & 3;           // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;            // column groups g with g % 2 == half
+    const int row_in_tile = quad * 32 + lane;
+    for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+      const GemmItem it = items[ii];
+      const MmaBlock b = blocks[it.block];
+      const DevGrid& g = grids[b.grid];
+      const int64_t K = g.K;
+      const int nt = min(kTileN, b.n - it.tn * kTileN), ntp = (nt + 15) & ~15;
+      const int r0 = it.tm * kM, c0 = it.tn * kTileN;
+      const int64_t nchunk = (K + kChunk - 1) / kChunk;
+      const int64_t per = (nchunk + b.n_ranges - 1) / b.n_ranges;
+      const int64_t ch0 = (int64_t)it.chunk * per, ch1 = min(nchunk, ch0 + per);
+      float H[32], L[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) { H[j] = 0.0f; L[j] = 0.0f; }
+      bool ok = true;
+      for (int64_t ch = ch0; ch < ch1; ++ch, ++c) {
+        const int st = c & 1;
+        ok = mbar_wait(smem_u32(&sm.full[st]), (c >> 1) & 1);
+        if (!ok) { *(volatile int*)&sm.abort = 1; atomicExch(status, 3); break; }
+        fence_after();
+        const int ea = sm.ea[st][row_in_tile];
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)st * 256u;
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi) {
+          const int gq = 2 * gi + half;  // 16-column group
+          if (gq * 16 < ntp) {
+            float hi[16], lo[16], d[16];
+            tmem_ld16(lane_base + 0 * ntp + gq * 16, hi);
+            tmem_ld16(lane_base + 1 * ntp + gq * 16, lo);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) lo[j] *= 0.00390625f;
+#pragma unroll
+            for (int ord = 2; ord < kSlices; ++ord) {
+              tmem_ld16(lane_base + ord * ntp + gq * 16, d);
+              tmem_wait_ld();
+              const float sc = pow2f(-8 * ord);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) lo[j] = fmaf(d[j], sc, lo[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float s = pow2f(ea + sm.eb[st][gq * 16 + j] - 14);
+              const float x = hi[j] * s;
+              const int q = gi * 16 + j;
+              const float t = H[q] + x;
+              const float bb = t - H[q];
+              const float err = (H[q] - (t - bb)) + (x - bb);
+              H[q] = t;
+              L[q] += fmaf(lo[j], s, err);
+            }
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) ws::mbar_arrive(smem_u32(&sm.freed[st]));
+      }
+      if (!ok) break;
+      // (hi, lo) partial sums of this item's point range
+      const int grow = r0 + row_in_tile;
+      if (grow < b.m) {
+        float2* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n;
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi) {
+          const int gq = 2 * gi + half;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int c = gq * 16 + j;
-            const float s = pow2f(ea + sm.eb[c] - 14);
-            const float x = hi[j] * s;
-            const float t = H[c] + x;
-            const float bb = t - H[c];
-            const float err = (H[c] - (t - bb)) + (x - bb);
-            H[c] = t;
-            L[c] += fmaf(lo[j], s, err);
+            const int col = gq * 16 + j;
+            if (col < nt) {
+              const float2 val = make_float2(H[gi * 16 + j], L[gi * 16 + j]);
+              if (b.transpose_out) out[(int64_t)(c0 + col) * b.m + grow] = val;
+              else out[(int64_t)grow * b.n + c0 + col] = val;
+            }
           }
         }
-      }
-    }
-    fence_before();
-    __syncthreads();
-  }
-  // ---- write this item's partial sums (FP64), times the FP64 constants of its row and column
-  if (ok && row < b.m) {
-    const double* rc = rowc + g.rc_off;
-    double ca;
-    if (b.a_mode == 1) ca = rc[b.a_row + pr.x] * rc[b.a_row + pr.y];
-    else ca = rc[b.a_row + row] * (b.a_w >= 0 ? rc[b.a_w] : 1.0);
-    const double cw = b.b_w >= 0 ? rc[b.b_w] : 1.0;
-    double* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n;
-#pragma unroll
-    for (int c = 0; c < kTileN; ++c) {
-      if (c < nt) {
-        const double val = ((double)H[c] + (double)L[c]) * ca * (rc[b.b_row + c0 + c] * cw);
-        if (b.transpose_out) out[(int64_t)(c0 + c) * b.m + row] = val;
-        else out[(int64_t)row * b.n + c0 + c] = val;
       }
     }
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 8) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+  }
+}
+
+// FP64 reduction of the (hi, lo) range partials of the tensor-core blocks, times the FP64
+// constants of each element's row and column; one warp per element, fixed order.
+__global__ void __launch_bounds__(256) reduce_mixed_kernel(const DevGrid* __restrict__ grids,
+                                                           const MmaBlock* __restrict__ blocks, int n_blocks,
+                                                           const int64_t* __restrict__ elem_begin, int64_t n_elems,
+                                                           const short2* __restrict__ pairs,
+                                                           const double* __restrict__ rowc,
+                                                           const float2* __restrict__ part, double* __restrict__ res) {
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= n_elems) return;
+  int lo = 0, hi = n_blocks;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (elem_begin[mid] <= wid) lo = mid; else hi = mid;
+  }
+  const MmaBlock b = blocks[lo];
+  const int64_t e = wid - elem_begin[lo];
+  const int64_t mn = (int64_t)b.m * b.n;
+  double s = 0.0;
+  for (int c = lane; c < b.n_ranges; c += 32) {
+    const float2 v = part[b.part_off + c * mn + e];
+    s += (double)v.x + (double)v.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    int r, col;  // A-side row, B-side column of element e
+    if (b.transpose_out) { col = (int)(e / b.m); r = (int)(e % b.m); }
+    else { r = (int)(e / b.n); col = (int)(e % b.n); }
+    const double* rc = rowc + grids[b.grid].rc_off;
+    double ca;
+    if (b.a_mode == 1) {
+      const short2 pr = pairs[b.pair_off + r];
+      ca = rc[b.a_row + pr.x] * rc[b.a_row + pr.y];
+    } else {
+      ca = rc[b.a_row + r] * (b.a_w >= 0 ? rc[b.a_w] : 1.0);
+    }
+    const double cb = rc[b.b_row + col] * (b.b_w >= 0 ? rc[b.b_w] : 1.0);
+    res[b.res_off + e] = s * ca * cb;
   }
 }
 
@@ -671,21 +782,32 @@ cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const
   return cudaGetLastError();
 }
 
-size_t mma_smem_bytes() { return sizeof(mma::Smem) + 1024; }
+size_t ws_smem_bytes() { return sizeof(ws::Smem) + 1024; }
 
-cudaError_t launch_contract_mma(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                                const short2* pairs, const float* ops, const double* rowc, double* part,
-                                int* status, cudaStream_t s) {
+cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
+                               int n_ctas, const short2* pairs, const float* ops, float2* part, int* status,
+                               cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   static bool attr_set = false;
-  const size_t bytes = mma_smem_bytes();
+  const size_t bytes = ws_smem_bytes();
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(contract_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(contract_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  contract_mma_kernel<<<n_items, mma::kThreads, bytes, s>>>(grids, blocks, items, pairs, ops, rowc, part, status);
+  contract_ws_kernel<<<n_ctas, ws::kThreads, bytes, s>>>(grids, blocks, items, n_items, pairs, ops, part, status);
   return cudaGetLastError();
 }
+
+cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
+                                int64_t n_elems, const short2* pairs, const double* rowc, const float2* part,
+                                double* res, cudaStream_t s) {
+  if (n_elems == 0) return cudaSuccess;
+  const int64_t threads = n_elems * 32;
+  reduce_mixed_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(grids, blocks, n_blocks, elem_begin, n_elems,
+                                                                         pairs, rowc, part, res);
+  return cudaGetLastError();
+}
+
 
 }  // namespace psq
