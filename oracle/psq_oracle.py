@@ -495,13 +495,15 @@ class _GridCache:
         return self.vals[k]
 
 
-def compute(job, mask=None, with_abs=True, j3_triples=None):
+def compute(job, mask=None, with_abs=True, j3_triples=None, pairs=None, aux_pairs=None):
     """All requested integral matrices of a job on their PS grids, FP64.
 
     Returns {"S","T","V": (n_bf, n_bf), "J2": (n_aux, n_aux), "J3": (n_aux, n_bf, n_bf)}
     for the classes in ``mask``, and with ``with_abs`` the matching sums of absolute terms
     (keys "absS", ...) that measure how much cancellation each element's sum carries.
-    ``j3_triples`` restricts J3 to the listed (C_aux, A, B) atom blocks (others stay 0).
+    ``j3_triples`` restricts J3 to the listed (C_aux, A, B) atom blocks, ``pairs`` restricts
+    S, T, V to the listed (A, B) atom blocks and ``aux_pairs`` J2 to the listed (C, D) blocks
+    (A <= B, C <= D; the other blocks stay 0).
     Quadrature per block is eq 9: sum_p w_p f(p) O(p) g(p).
     """
     mask = job.mask if mask is None else mask
@@ -539,6 +541,8 @@ def compute(job, mask=None, with_abs=True, j3_triples=None):
     for A in range(nat):
         for B in range(A, nat):
             if bcount[A] == 0 or bcount[B] == 0:
+                continue
+            if pairs is not None and (A, B) not in pairs:
                 continue
             if mask & (S | T):
                 key = grid_key(job.atoms, A, B, A)
@@ -581,6 +585,8 @@ def compute(job, mask=None, with_abs=True, j3_triples=None):
         for C in range(nat):
             for D in range(C, nat):
                 if acount[C] == 0 or acount[D] == 0:
+                    continue
+                if aux_pairs is not None and (C, D) not in aux_pairs:
                     continue
                 key = grid_key(job.atoms, C, D, C)
                 g = cache.grid(key)

@@ -373,127 +373,262 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     ops += (int64_t)rows * g.ld;
     P.n_points += g.K;
   }
-  // contraction blocks
-  std::vector<int64_t> s_loc(P.grids.size(), -1), t_loc(P.grids.size(), -1), va_loc(P.grids.size(), -1),
-      vb_loc(P.grids.size(), -1), vc_loc(P.grids.size(), -1), j2_loc(P.grids.size(), -1);
-  std::map<std::tuple<int, int, int>, J3Src> j3blk;
-  int64_t res = 0;
-  auto add_block = [&](int g, int a_row, int m, int b_row, int n, int b_mode, int pair_off, int d_row) {
-    GemmBlock b{};
-    b.grid = g; b.a_row = a_row; b.m = m; b.b_row = b_row; b.n = n; b.b_mode = b_mode;
-    b.pair_off = pair_off; b.d_row = d_row; b.res_off = res;
-    res += (int64_t)m * n;
-    P.gblocks.push_back(b);
-    return b.res_off;
-  };
-  for (size_t gi = 0; gi < P.grids.size(); ++gi) {
-    DevGrid& g = P.grids[gi];
-    const int nl = g.nFA + g.nFB;
-    const int w = g.row_W;
-    const int gint = (int)gi;
-    if (g.C < 0) {
-      if (nl > 0) {
-        if (mask & PSQ_S) s_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w);
-        if (mask & PSQ_T) t_loc[gi] = add_block(gint, g.row_F, nl, g.row_L, nl, 0, 0, w);
-        if (mask & PSQ_V) {
-          va_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 1);
-          vb_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 2);
-        }
-      }
-      if ((mask & PSQ_J2) && g.nG > 0) j2_loc[gi] = add_block(gint, g.row_U, g.nG, g.row_G, g.nG, 0, 0, w);
-      if (mask & PSQ_J3) {
-        const int atoms2[2] = {g.A, g.B};
-        for (int xi = 0; xi < 2; ++xi) {
-          const int X = atoms2[xi];
-          if (j->na[X] == 0) continue;
-          const int aoff = xi == 0 ? 0 : j->na[g.A];
-          const int yw[3][2] = {{g.A, g.A}, {g.A, g.B}, {g.B, g.B}};
-          for (auto& p : yw) {
-            const int Y = p[0], W = p[1];
-            if (j->nb[Y] == 0 || j->nb[W] == 0) continue;
-            const GridKey k = grid_for(j, Y, W, X);
-            if (k.A != g.A || k.B != g.B || k.C != -1) continue;
-            const int yoff = Y == g.A ? 0 : g.nFA, woff = W == g.A ? 0 : g.nFA;
-            const int pair_off = (int)P.pairs.size();
-            if (Y != W) {
-              for (int i = 0; i < j->nb[Y]; ++i)
-                for (int jj = 0; jj < j->nb[W]; ++jj) P.pairs.push_back(make_short2(yoff + i, woff + jj));
-            } else {
-              for (int i = 0; i < j->nb[Y]; ++i)
-                for (int jj = i; jj < j->nb[Y]; ++jj) P.pairs.push_back(make_short2(yoff + i, yoff + jj));
-            }
-            const int np = (int)P.pairs.size() - pair_off;
-            const int64_t off = add_block(gint, g.row_U + aoff, j->na[X], g.row_F, np, 1, pair_off, w);
-            j3blk[{X, Y, W}] = J3Src{off, np, j->nb[W], Y == W ? 1 : 0, 0};
+  // contraction blocks and assembly sources
+  int64_t res = 0, part = 0;
+  auto local_off = [&](const DevGrid& g, int X) { return X == g.A ? 0 : g.nFA; };
+  auto aux_off = [&](const DevGrid& g, int X) { return X == g.A ? 0 : j->na[g.A]; };
+  for (int c = 0; c < 4; ++c) P.src_ptr[c].assign(nat * nat + 1, 0);
+  P.j3.assign((size_t)nat * nat * nat, J3Src{0, 0, 0, 0, 0, 0, 0});
+  auto J3at = [&](int X, int Y, int W) -> J3Src& { return P.j3[((size_t)X * nat + Y) * nat + W]; };
+  if (!P.mixed) {
+    // FP64 path: one block per (grid, class) and per (grid, aux atom, basis atom pair)
+    std::vector<int64_t> s_loc(P.grids.size(), -1), t_loc(P.grids.size(), -1), va_loc(P.grids.size(), -1),
+        vb_loc(P.grids.size(), -1), vc_loc(P.grids.size(), -1), j2_loc(P.grids.size(), -1);
+    auto add_block = [&](int g, int a_row, int m, int b_row, int n, int b_mode, int pair_off, int d_row) {
+      GemmBlock b{};
+      b.grid = g; b.a_row = a_row; b.m = m; b.b_row = b_row; b.n = n; b.b_mode = b_mode;
+      b.pair_off = pair_off; b.d_row = d_row; b.res_off = res;
+      res += (int64_t)m * n;
+      P.gblocks.push_back(b);
+      return b.res_off;
+    };
+    for (size_t gi = 0; gi < P.grids.size(); ++gi) {
+      DevGrid& g = P.grids[gi];
+      const int nl = g.nFA + g.nFB;
+      const int w = g.row_W;
+      const int gint = (int)gi;
+      if (g.C < 0) {
+        if (nl > 0) {
+          if (mask & PSQ_S) s_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w);
+          if (mask & PSQ_T) t_loc[gi] = add_block(gint, g.row_F, nl, g.row_L, nl, 0, 0, w);
+          if (mask & PSQ_V) {
+            va_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 1);
+            vb_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 2);
           }
         }
-      }
-    } else {
-      if ((mask & PSQ_V) && g.nFA > 0 && g.nFB > 0)
-        vc_loc[gi] = add_block(gint, g.row_F, g.nFA, g.row_F + g.nFA, g.nFB, 0, 0, w + 3);
-      if ((mask & PSQ_J3) && j->na[g.C] > 0 && g.nFA > 0 && g.nFB > 0) {
-        const int pair_off = (int)P.pairs.size();
-        for (int i = 0; i < g.nFA; ++i)
-          for (int jj = 0; jj < g.nFB; ++jj) P.pairs.push_back(make_short2(i, g.nFA + jj));
-        const int np = g.nFA * g.nFB;
-        const int64_t off = add_block(gint, g.row_U, j->na[g.C], g.row_F, np, 1, pair_off, w);
-        j3blk[{g.C, g.A, g.B}] = J3Src{off, np, g.nFB, 0, 0};
-      }
-    }
-  }
-  // chunking: enough CTAs for several waves, chunks of at least 2048 points
-  int64_t tiles = 0;
-  for (auto& b : P.gblocks) tiles += (int64_t)((b.m + kTile - 1) / kTile) * ((b.n + kTile - 1) / kTile);
-  const int64_t want = 2LL * kSmCount * 8;
-  const int cglob = (int)std::max<int64_t>(1, tiles > 0 ? (want + tiles - 1) / tiles : 1);
-  int64_t part = 0;
-  for (size_t bi = 0; bi < P.gblocks.size(); ++bi) {
-    GemmBlock& b = P.gblocks[bi];
-    const int64_t K = P.grids[b.grid].K;
-    b.n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(cglob, (K + 2047) / 2048));
-    b.part_off = part;
-    part += (int64_t)b.n_chunks * b.m * b.n;
-    const int tm = (b.m + kTile - 1) / kTile, tn = (b.n + kTile - 1) / kTile;
-    for (int c = 0; c < b.n_chunks; ++c)
-      for (int x = 0; x < tm; ++x)
-        for (int y = 0; y < tn; ++y) P.items.push_back(GemmItem{(int)bi, x, y, c});
-  }
-  if (P.mixed) {
-    // tensor-core blocks: the bigger / product side as the 128-row A operand
-    P.items.clear();
-    int64_t mtiles = 0;
-    for (auto& b : P.gblocks) {
-      MmaBlock mb{};
-      mb.grid = b.grid;
-      mb.res_off = b.res_off;
-      if (b.b_mode == 1) {
-        mb.m = b.n; mb.n = b.m; mb.a_mode = 1; mb.a_row = b.b_row; mb.a_w = -1; mb.pair_off = b.pair_off;
-        mb.b_row = b.a_row; mb.b_w = b.d_row; mb.transpose_out = 1;
+        if ((mask & PSQ_J2) && g.nG > 0) j2_loc[gi] = add_block(gint, g.row_U, g.nG, g.row_G, g.nG, 0, 0, w);
+        if (mask & PSQ_J3) {
+          const int atoms2[2] = {g.A, g.B};
+          for (int xi = 0; xi < 2; ++xi) {
+            const int X = atoms2[xi];
+            if (j->na[X] == 0) continue;
+            const int aoff = xi == 0 ? 0 : j->na[g.A];
+            const int yw[3][2] = {{g.A, g.A}, {g.A, g.B}, {g.B, g.B}};
+            for (auto& pq : yw) {
+              const int Y = pq[0], W = pq[1];
+              if (j->nb[Y] == 0 || j->nb[W] == 0) continue;
+              const GridKey k = grid_for(j, Y, W, X);
+              if (k.A != g.A || k.B != g.B || k.C != -1) continue;
+              const int yoff = Y == g.A ? 0 : g.nFA, woff = W == g.A ? 0 : g.nFA;
+              const int pair_off = (int)P.pairs.size();
+              if (Y != W) {
+                for (int i = 0; i < j->nb[Y]; ++i)
+                  for (int jj = 0; jj < j->nb[W]; ++jj) P.pairs.push_back(make_short2(yoff + i, woff + jj));
+              } else {
+                for (int i = 0; i < j->nb[Y]; ++i)
+                  for (int jj = i; jj < j->nb[Y]; ++jj) P.pairs.push_back(make_short2(yoff + i, yoff + jj));
+              }
+              const int np = (int)P.pairs.size() - pair_off;
+              const int64_t off = add_block(gint, g.row_U + aoff, j->na[X], g.row_F, np, 1, pair_off, w);
+              J3at(X, Y, W) = J3Src{off, 1, np, Y == W ? 1 : 0, Y == W ? j->nb[Y] : j->nb[W], 0, 0};
+            }
+          }
+        }
       } else {
-        mb.m = b.m; mb.n = b.n; mb.a_mode = 0; mb.a_row = b.a_row; mb.a_w = -1; mb.pair_off = 0;
-        mb.b_row = b.b_row; mb.b_w = b.d_row; mb.transpose_out = 0;
+        if ((mask & PSQ_V) && g.nFA > 0 && g.nFB > 0)
+          vc_loc[gi] = add_block(gint, g.row_F, g.nFA, g.row_F + g.nFA, g.nFB, 0, 0, w + 3);
+        if ((mask & PSQ_J3) && j->na[g.C] > 0 && g.nFA > 0 && g.nFB > 0) {
+          const int pair_off = (int)P.pairs.size();
+          for (int i = 0; i < g.nFA; ++i)
+            for (int jj = 0; jj < g.nFB; ++jj) P.pairs.push_back(make_short2(i, g.nFA + jj));
+          const int np = g.nFA * g.nFB;
+          const int64_t off = add_block(gint, g.row_U, j->na[g.C], g.row_F, np, 1, pair_off, w);
+          J3at(g.C, g.A, g.B) = J3Src{off, 1, np, 0, g.nFB, 0, 0};
+        }
       }
-      mtiles += (int64_t)((mb.m + 127) / 128) * ((mb.n + 63) / 64);
-      P.mblocks.push_back(mb);
     }
+    // chunking: enough CTAs for several waves, chunks of at least 2048 points
+    int64_t tiles = 0;
+    for (auto& b : P.gblocks) tiles += (int64_t)((b.m + kTile - 1) / kTile) * ((b.n + kTile - 1) / kTile);
+    const int64_t want = 2LL * kSmCount * 8;
+    const int cglob = (int)std::max<int64_t>(1, tiles > 0 ? (want + tiles - 1) / tiles : 1);
+    for (size_t bi = 0; bi < P.gblocks.size(); ++bi) {
+      GemmBlock& b = P.gblocks[bi];
+      const int64_t K = P.grids[b.grid].K;
+      b.n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(cglob, (K + 2047) / 2048));
+      b.part_off = part;
+      part += (int64_t)b.n_chunks * b.m * b.n;
+      const int tm = (b.m + kTile - 1) / kTile, tn = (b.n + kTile - 1) / kTile;
+      for (int c = 0; c < b.n_chunks; ++c)
+        for (int x = 0; x < tm; ++x)
+          for (int y = 0; y < tn; ++y) P.items.push_back(GemmItem{(int)bi, x, y, c});
+    }
+    P.elem_begin.resize(P.gblocks.size() + 1);
+    P.elem_begin[0] = 0;
+    for (size_t bi = 0; bi < P.gblocks.size(); ++bi)
+      P.elem_begin[bi + 1] = P.elem_begin[bi] + (int64_t)P.gblocks[bi].m * P.gblocks[bi].n;
+    for (int X = 0; X < nat; ++X) {
+      for (int Y = 0; Y < nat; ++Y) {
+        for (int c = 0; c < 4; ++c) P.src_ptr[c][X * nat + Y] = (int)P.src[c].size();
+        if (X > Y || mask == 0) continue;
+        const int gb = gidx[grid_for(j, X, Y, X)];
+        const DevGrid& G = P.grids[gb];
+        const int nl = G.nFA + G.nFB, oX = local_off(G, X), oY = local_off(G, Y);
+        if (mask & PSQ_S) P.src[0].push_back(SrcEntry{s_loc[gb], nl, oX, oY, oY, oX, 0, 0, 0, 1.0});
+        if (mask & PSQ_T) P.src[1].push_back(SrcEntry{t_loc[gb], nl, oX, oY, oY, oX, 0, 0, 0, 1.0});
+        if (mask & PSQ_V) {
+          for (int C = 0; C < nat; ++C) {
+            const GridKey k = grid_for(j, X, Y, C);
+            const int gv = gidx[k];
+            const DevGrid& H = P.grids[gv];
+            const double z = -(double)j->atoms[C].Z;
+            if (k.C >= 0) {
+              P.src[2].push_back(SrcEntry{vc_loc[gv], H.nFB, 0, 0, 0, 0, 0, 0, 0, z});
+            } else {
+              const int64_t off = C == H.A ? va_loc[gv] : vb_loc[gv];
+              const int hX = local_off(H, X), hY = local_off(H, Y);
+              P.src[2].push_back(SrcEntry{off, H.nFA + H.nFB, hX, hY, hY, hX, 0, 0, 0, z});
+            }
+          }
+        }
+        if (mask & PSQ_J2) {
+          const int aX = aux_off(G, X), aY = aux_off(G, Y);
+          P.src[3].push_back(SrcEntry{j2_loc[gb], G.nG, aX, aY, aY, aX, 0, 0, 0, 1.0});
+        }
+      }
+    }
+  } else {
+    // Tensor-core path: per grid one pair block (all local pairs chi_i chi_j against the
+    // weighted aux potentials and the plain weights w, w/r_A, w/r_B or w/r_C, giving J3, S
+    // and V together), one kinetic block and one (P|Q) block.
+    struct GridBlocks { int pair = -1, kin = -1, j2 = -1, colS = -1, colVA = -1, colVB = -1, colVC = -1; };
+    std::vector<GridBlocks> gbk(P.grids.size());
+    auto add_mblock = [&](int g, int m, int n, int a_off, int b_off) {
+      MmaBlock b{};
+      b.grid = g; b.m = m; b.n = n; b.a_off = a_off; b.b_off = b_off; b.res_off = res;
+      res += (int64_t)m * n;
+      P.mblocks.push_back(b);
+      return (int)P.mblocks.size() - 1;
+    };
+    for (size_t gi = 0; gi < P.grids.size(); ++gi) {
+      const DevGrid& g = P.grids[gi];
+      const int nl = g.nFA + g.nFB, W = g.row_W;
+      GridBlocks& gb = gbk[gi];
+      if (g.C < 0) {
+        const bool j3 = (mask & PSQ_J3) && g.nG > 0;
+        if (nl > 0 && (j3 || (mask & (PSQ_S | PSQ_V)))) {
+          const int a_off = (int)P.pairs.size();
+          for (int i = 0; i < nl; ++i)
+            for (int jj = i; jj < nl; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + jj));
+          const int b_off = (int)P.pairs.size();
+          if (j3)
+            for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
+          if (mask & PSQ_S) { gb.colS = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W, -1)); }
+          if (mask & PSQ_V) {
+            gb.colVA = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W + 1, -1));
+            gb.colVB = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W + 2, -1));
+          }
+          gb.pair = add_mblock((int)gi, nl * (nl + 1) / 2, (int)P.pairs.size() - b_off, a_off, b_off);
+        }
+        if ((mask & PSQ_T) && nl > 0) {
+          const int a_off = (int)P.pairs.size();
+          for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_F + i, -1));
+          const int b_off = (int)P.pairs.size();
+          for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_L + i, W));
+          gb.kin = add_mblock((int)gi, nl, nl, a_off, b_off);
+        }
+        if ((mask & PSQ_J2) && g.nG > 0) {
+          const int a_off = (int)P.pairs.size();
+          for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_G + q, -1));
+          const int b_off = (int)P.pairs.size();
+          for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
+          gb.j2 = add_mblock((int)gi, g.nG, g.nG, a_off, b_off);
+        }
+      } else if (g.nFA > 0 && g.nFB > 0) {
+        const bool j3 = (mask & PSQ_J3) && g.nG > 0;
+        if (j3 || (mask & PSQ_V)) {
+          const int a_off = (int)P.pairs.size();
+          for (int i = 0; i < g.nFA; ++i)
+            for (int jj = 0; jj < g.nFB; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + g.nFA + jj));
+          const int b_off = (int)P.pairs.size();
+          if (j3)
+            for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
+          if (mask & PSQ_V) { gb.colVC = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W + 3, -1)); }
+          gb.pair = add_mblock((int)gi, g.nFA * g.nFB, (int)P.pairs.size() - b_off, a_off, b_off);
+        }
+      }
+    }
+    // assembly sources
+    auto blk = [&](int b) -> const MmaBlock& { return P.mblocks[b]; };
+    for (int X = 0; X < nat; ++X) {
+      for (int Y = 0; Y < nat; ++Y) {
+        for (int c = 0; c < 4; ++c) P.src_ptr[c][X * nat + Y] = (int)P.src[c].size();
+        if (X > Y || mask == 0) continue;
+        const int gi = gidx[grid_for(j, X, Y, X)];
+        const DevGrid& G = P.grids[gi];
+        const GridBlocks& gb = gbk[gi];
+        const int nl = G.nFA + G.nFB, oX = local_off(G, X), oY = local_off(G, Y);
+        if ((mask & PSQ_S) && gb.pair >= 0)
+          P.src[0].push_back(SrcEntry{blk(gb.pair).res_off, blk(gb.pair).n, oX, oY, 0, gb.colS, 1, nl, 0, 1.0});
+        if ((mask & PSQ_T) && gb.kin >= 0)
+          P.src[1].push_back(SrcEntry{blk(gb.kin).res_off, nl, oX, oY, oY, oX, 0, 0, 0, 1.0});
+        if (mask & PSQ_V) {
+          for (int C = 0; C < nat; ++C) {
+            const GridKey k = grid_for(j, X, Y, C);
+            const int hv = gidx[k];
+            const DevGrid& H = P.grids[hv];
+            const GridBlocks& hb = gbk[hv];
+            if (hb.pair < 0) continue;
+            const double z = -(double)j->atoms[C].Z;
+            if (k.C >= 0) {
+              P.src[2].push_back(SrcEntry{blk(hb.pair).res_off, blk(hb.pair).n, 0, 0, 0, hb.colVC, 2, H.nFB, 0, z});
+            } else {
+              const int col = C == H.A ? hb.colVA : hb.colVB;
+              P.src[2].push_back(SrcEntry{blk(hb.pair).res_off, blk(hb.pair).n, local_off(H, X), local_off(H, Y), 0,
+                                          col, 1, H.nFA + H.nFB, 0, z});
+            }
+          }
+        }
+        if ((mask & PSQ_J2) && gb.j2 >= 0) {
+          const int aX = aux_off(G, X), aY = aux_off(G, Y);
+          P.src[3].push_back(SrcEntry{blk(gb.j2).res_off, G.nG, aX, aY, aY, aX, 0, 0, 0, 1.0});
+        }
+      }
+    }
+    if (mask & PSQ_J3) {
+      for (int X = 0; X < nat; ++X)
+        for (int Y = 0; Y < nat; ++Y)
+          for (int W = Y; W < nat; ++W) {
+            if (j->na[X] == 0 || j->nb[Y] == 0 || j->nb[W] == 0) continue;
+            const GridKey k = grid_for(j, Y, W, X);
+            const int gi = gidx[k];
+            const DevGrid& G = P.grids[gi];
+            const GridBlocks& gb = gbk[gi];
+            if (gb.pair < 0) continue;
+            const MmaBlock& b = blk(gb.pair);
+            if (k.C >= 0)
+              J3at(X, Y, W) = J3Src{b.res_off, b.n, 1, 0, G.nFB, 0, 0};
+            else
+              J3at(X, Y, W) = J3Src{b.res_off + aux_off(G, X), b.n, 1, 1, G.nFA + G.nFB, local_off(G, Y),
+                                    local_off(G, W)};
+          }
+    }
+    // work items: 128 x 64 tiles of every block, its point range cut for load balance
+    int64_t mtiles = 0;
+    for (auto& mb : P.mblocks) mtiles += (int64_t)((mb.m + 127) / 128) * ((mb.n + 63) / 64);
     const int64_t want = 4LL * kSmCount;
     const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
-    part = 0;
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi) {
       MmaBlock& mb = P.mblocks[bi];
-      GemmBlock& gb = P.gblocks[bi];
       const int64_t nch = (P.grids[mb.grid].K + 63) / 64;
       mb.n_ranges = (int)std::max<int64_t>(1, std::min<int64_t>(cr, (nch + 15) / 16));
       mb.part_off = part;
-      gb.n_chunks = mb.n_ranges;
-      gb.part_off = part;
       part += (int64_t)mb.n_ranges * mb.m * mb.n;
       const int tm = (mb.m + 127) / 128, tn = (mb.n + 63) / 64;
       for (int c = 0; c < mb.n_ranges; ++c)
         for (int x = 0; x < tm; ++x)
           for (int y = 0; y < tn; ++y) P.mitems.push_back(GemmItem{(int)bi, x, y, c});
     }
-    // longest items first: the persistent CTAs take them round-robin
     auto item_chunks = [&](const GemmItem& it) {
       const MmaBlock& mb = P.mblocks[it.block];
       const int64_t nch = (P.grids[mb.grid].K + 63) / 64;
@@ -502,6 +637,13 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     };
     std::stable_sort(P.mitems.begin(), P.mitems.end(),
                      [&](const GemmItem& x, const GemmItem& y) { return item_chunks(x) > item_chunks(y); });
+    P.elem_begin.resize(P.mblocks.size() + 1);
+    P.elem_begin[0] = 0;
+    for (size_t bi = 0; bi < P.mblocks.size(); ++bi)
+      P.elem_begin[bi + 1] = P.elem_begin[bi] + (int64_t)P.mblocks[bi].m * P.mblocks[bi].n;
+  }
+  for (int c = 0; c < 4; ++c) P.src_ptr[c][nat * nat] = (int)P.src[c].size();
+  if (P.mixed) {
     // FP32-pair rotation, x-scales of the shells and FP64 row constants
     auto klm = [](int l, int m) {
       const int am = std::abs(m);
@@ -571,49 +713,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       P.max_node_entries = std::max(P.max_node_entries, n);
     }
   }
-  P.elem_begin.resize(P.gblocks.size() + 1);
-  P.elem_begin[0] = 0;
-  for (size_t bi = 0; bi < P.gblocks.size(); ++bi)
-    P.elem_begin[bi + 1] = P.elem_begin[bi] + (int64_t)P.gblocks[bi].m * P.gblocks[bi].n;
   for (size_t gi = 0; gi < P.grids.size(); ++gi)
     for (int64_t p0 = 0; p0 < P.grids[gi].K; p0 += kPointsPerBlock) P.pblocks.push_back(PointBlock{(int)gi, 0, p0});
-  // assembly sources (S, T, V, J2 in slots 0..3)
-  auto local_off = [&](const DevGrid& g, int X) { return X == g.A ? 0 : g.nFA; };
-  auto aux_off = [&](const DevGrid& g, int X) { return X == g.A ? 0 : j->na[g.A]; };
-  for (int c = 0; c < 4; ++c) P.src_ptr[c].assign(nat * nat + 1, 0);
-  for (int X = 0; X < nat; ++X) {
-    for (int Y = 0; Y < nat; ++Y) {
-      for (int c = 0; c < 4; ++c) P.src_ptr[c][X * nat + Y] = (int)P.src[c].size();
-      if (X > Y || mask == 0) continue;
-      const GridKey kb = grid_for(j, X, Y, X);
-      const int gb = gidx[kb];
-      const DevGrid& G = P.grids[gb];
-      const int nl = G.nFA + G.nFB;
-      if (mask & PSQ_S) P.src[0].push_back(SrcEntry{s_loc[gb], nl, local_off(G, X), local_off(G, Y), 1.0});
-      if (mask & PSQ_T) P.src[1].push_back(SrcEntry{t_loc[gb], nl, local_off(G, X), local_off(G, Y), 1.0});
-      if (mask & PSQ_V) {
-        for (int C = 0; C < nat; ++C) {
-          const GridKey k = grid_for(j, X, Y, C);
-          const int gv = gidx[k];
-          const DevGrid& H = P.grids[gv];
-          const double z = -(double)j->atoms[C].Z;
-          if (k.C >= 0) {
-            P.src[2].push_back(SrcEntry{vc_loc[gv], H.nFB, 0, 0, z});
-          } else {
-            const int64_t off = C == H.A ? va_loc[gv] : vb_loc[gv];
-            P.src[2].push_back(SrcEntry{off, H.nFA + H.nFB, local_off(H, X), local_off(H, Y), z});
-          }
-        }
-      }
-      if (mask & PSQ_J2) P.src[3].push_back(SrcEntry{j2_loc[gb], G.nG, aux_off(G, X), aux_off(G, Y), 1.0});
-    }
-  }
-  for (int c = 0; c < 4; ++c) P.src_ptr[c][nat * nat] = (int)P.src[c].size();
-  P.j3.assign((size_t)nat * nat * nat, J3Src{0, 0, 0, 0, 0});
-  for (auto& kv : j3blk) {
-    const int X = std::get<0>(kv.first), Y = std::get<1>(kv.first), W = std::get<2>(kv.first);
-    P.j3[((size_t)X * nat + Y) * nat + W] = kv.second;
-  }
   // useful contractions: for every molecule-matrix block, rows x cols x the live points of
   // the one grid that integrates it (same-atom blocks count i <= j once)
   P.contractions = 0;

@@ -54,17 +54,15 @@ struct DevGrid {
 // sine/cosine (sinh/cosh for mu), sin^2(v/2) (sinh^2 for mu), cos^2(v/2), and the 1-D weight.
 struct NodeEntry { double v, s, c, h2, g2, w; };
 
-// A contraction block of the tensor-core path: out = sum_p A_r(p) B_c(p) with
-// A_r = src[a_row + r] (* src[a_w]) or, a_mode 1, src[a_row + i] * src[a_row + j] for pair r,
-// and B_c = src[b_row + c] (* src[b_w]).  transpose_out stores the m x n result as [c][r].
+// A contraction block of the tensor-core path: R[r][c] = sum_p A_r(p) B_c(p), row-major
+// m x n, where every operand row is one of the grid's operand rows times an optional second
+// one: A_r = src[a.x] * src[a.y] (a = rows[a_off + r], y = -1: no factor), B_c likewise from
+// rows[b_off + c].  This covers pair products chi_i chi_j and weighted rows w chi, w V^P.
 struct MmaBlock {
   int grid;
   int m, n;
-  int a_mode, a_row, a_w, pair_off;
-  int b_row, b_w;
-  int transpose_out;
+  int a_off, b_off;
   int n_ranges;
-  int pad;
   int64_t res_off, part_off;
 };
 
@@ -86,8 +84,20 @@ struct GemmBlock {
 struct GemmItem { int block, tm, tn, chunk; };
 
 // Assembly sources (Section 4: each element from exactly one grid, V_ne summed over nuclei).
-struct SrcEntry { int64_t off; int ld, row0, col0; double z; };
-struct J3Src { int64_t off; int npairs, nW, packed, pad; };
+// Two-index element (a on X, b on Y, local indices la, lb) from block M = res + off:
+//   mode 0: M[(rX+la)*ld + cY+lb], averaged with its mirror M[(rY+lb)*ld + cX+la] where the
+//           class is symmetrised;
+//   mode 1: M[p*ld + cX], p = packed index of the local pair (rX+la, cY+lb) over nloc;
+//   mode 2: M[p*ld + cX], p = la*nloc + lb (a rectangular pair list).
+struct SrcEntry {
+  int64_t off;
+  int ld, rX, cY, rY, cX, mode, nloc, pad;
+  double z;
+};
+// Three-index element (P on X, i on Y, j on W; Y <= W): res[off + p*s_pair + lP*s_aux] with
+// p the packed (mode 1) index of (offY+li, offW+lj) over nloc or (mode 0) (offY+li)*nloc +
+// offW+lj.
+struct J3Src { int64_t off; int s_pair, s_aux, mode, nloc, offY, offW; };
 
 struct PointBlock { int grid; int pad; int64_t p0; };  // evaluation: 256 points of one grid
 
@@ -127,10 +137,10 @@ cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const
                               cudaStream_t s);
 size_t ws_smem_bytes();
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                               int n_ctas, const short2* pairs, const float* ops, float2* part, int* status,
+                               int n_ctas, const short2* rows, const float* ops, float2* part, int* status,
                                cudaStream_t s);
 cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
-                                int64_t n_elems, const short2* pairs, const double* rowc, const float2* part,
+                                int64_t n_elems, const short2* rows, const double* rowc, const float2* part,
                                 double* res, cudaStream_t s);
 
 // Host side (psq_host.cpp): psq_compute on a given workspace; with plan_must_exist the call

@@ -380,13 +380,21 @@ __global__ void assemble2_kernel(int cls, int nat, int nfn, const int* __restric
   for (int e = src_ptr[X * nat + Y]; e < src_ptr[X * nat + Y + 1]; ++e) {
     const SrcEntry s = src[e];
     const double* M = res + s.off;
-    const double m1 = M[(int64_t)(s.row0 + la) * s.ld + s.col0 + lb];
-    if (cls == 2) {
-      v += -0.25 * (m1 + M[(int64_t)(s.col0 + lb) * s.ld + s.row0 + la]);
-    } else if (cls == 8 || X == Y) {
-      v += s.z * 0.5 * (m1 + M[(int64_t)(s.col0 + lb) * s.ld + s.row0 + la]);
+    if (s.mode == 0) {
+      const double m1 = M[(int64_t)(s.rX + la) * s.ld + s.cY + lb];
+      const double m2 = M[(int64_t)(s.rY + lb) * s.ld + s.cX + la];
+      if (cls == 2) v += -0.25 * (m1 + m2);
+      else if (cls == 8 || X == Y) v += s.z * 0.5 * (m1 + m2);
+      else v += s.z * m1;
     } else {
-      v += s.z * m1;
+      int64_t p;
+      if (s.mode == 1) {
+        const int i = min(s.rX + la, s.cY + lb), j = max(s.rX + la, s.cY + lb);
+        p = (int64_t)i * s.nloc - (int64_t)i * (i - 1) / 2 + (j - i);
+      } else {
+        p = (int64_t)la * s.nloc + lb;
+      }
+      v += s.z * M[p * s.ld + s.cX];
     }
   }
   out[idx] = v;
@@ -406,13 +414,14 @@ __global__ void assemble3_kernel(int nat, int nfn, int naux, const int* __restri
   if (Y > W) { int t = Y; Y = W; W = t; t = la; la = lb; lb = t; }
   const J3Src s = j3[((int64_t)X * nat + Y) * nat + W];
   int64_t pidx;
-  if (s.packed) {
-    const int i = min(la, lb), j = max(la, lb);
-    pidx = (int64_t)i * s.nW - (int64_t)i * (i - 1) / 2 + (j - i);
+  const int i0 = s.offY + la, j0 = s.offW + lb;
+  if (s.mode == 1) {
+    const int i = min(i0, j0), j = max(i0, j0);
+    pidx = (int64_t)i * s.nloc - (int64_t)i * (i - 1) / 2 + (j - i);
   } else {
-    pidx = (int64_t)la * s.nW + lb;
+    pidx = (int64_t)i0 * s.nloc + j0;
   }
-  out[idx] = res[s.off + (int64_t)lp * s.npairs + pidx];
+  out[idx] = res[s.off + pidx * s.s_pair + (int64_t)lp * s.s_aux];
 }
 
 cudaError_t launch_assemble(int cls, int nat, int nfn, int naux, const int* fn_atom,

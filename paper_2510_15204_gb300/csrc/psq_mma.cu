@@ -533,7 +533,7 @@ __device__ __forceinline__ void produce_half(const float* src, const float* mul,
 __global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevGrid* __restrict__ grids,
                                                                       const MmaBlock* __restrict__ blocks,
                                                                       const GemmItem* __restrict__ items, int n_items,
-                                                                      const short2* __restrict__ pairs,
+                                                                      const short2* __restrict__ rows,
                                                                       const float* __restrict__ ops,
                                                                       float2* __restrict__ part,
                                                                       int* __restrict__ status) {
@@ -575,25 +575,24 @@ __global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevG
       const int64_t per = (nchunk + b.n_ranges - 1) / b.n_ranges;
       const int64_t ch0 = (int64_t)it.chunk * per, ch1 = min(nchunk, ch0 + per);
       const uint32_t idesc = make_idesc(ntp);
-      // this thread's A task: row tid/2, half tid%2
+      // this thread's A task: row tid/2, half tid%2; B task (tid < 2 ntp): column tid/2
       const int arow = tid >> 1, ah = tid & 1;
       const int grow = r0 + arow;
       const bool avalid = grow < b.m;
       const float *asrc = nullptr, *amul = nullptr;
       if (avalid) {
-        if (b.a_mode == 1) {
-          const short2 pr = pairs[b.pair_off + grow];
-          asrc = base + (int64_t)(b.a_row + pr.x) * ld;
-          amul = base + (int64_t)(b.a_row + pr.y) * ld;
-        } else {
-          asrc = base + (int64_t)(b.a_row + grow) * ld;
-          amul = b.a_w >= 0 ? base + (int64_t)b.a_w * ld : nullptr;
-        }
+        const short2 q = rows[b.a_off + grow];
+        asrc = base + (int64_t)q.x * ld;
+        amul = q.y >= 0 ? base + (int64_t)q.y * ld : nullptr;
       }
       const int brow = tid >> 1;
       const bool btask = tid < 2 * ntp, bvalid = brow < nt;
-      const float* bsrc = bvalid ? base + (int64_t)(b.b_row + c0 + brow) * ld : nullptr;
-      const float* bmul = (bvalid && b.b_w >= 0) ? base + (int64_t)b.b_w * ld : nullptr;
+      const float *bsrc = nullptr, *bmul = nullptr;
+      if (bvalid) {
+        const short2 q = rows[b.b_off + c0 + brow];
+        bsrc = base + (int64_t)q.x * ld;
+        bmul = q.y >= 0 ? base + (int64_t)q.y * ld : nullptr;
+      }
       for (int64_t ch = ch0; ch < ch1; ++ch, ++c) {
         const int st = c & 1;
         bool ok = true;
@@ -705,9 +704,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevG
           for (int j = 0; j < 16; ++j) {
             const int col = gq * 16 + j;
             if (col < nt) {
-              const float2 val = make_float2(H[gi * 16 + j], L[gi * 16 + j]);
-              if (b.transpose_out) out[(int64_t)(c0 + col) * b.m + grow] = val;
-              else out[(int64_t)grow * b.n + c0 + col] = val;
+              out[(int64_t)grow * b.n + c0 + col] = make_float2(H[gi * 16 + j], L[gi * 16 + j]);
             }
           }
         }
@@ -727,7 +724,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevG
 __global__ void __launch_bounds__(256) reduce_mixed_kernel(const DevGrid* __restrict__ grids,
                                                            const MmaBlock* __restrict__ blocks, int n_blocks,
                                                            const int64_t* __restrict__ elem_begin, int64_t n_elems,
-                                                           const short2* __restrict__ pairs,
+                                                           const short2* __restrict__ rows,
                                                            const double* __restrict__ rowc,
                                                            const float2* __restrict__ part, double* __restrict__ res) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -749,18 +746,11 @@ __global__ void __launch_bounds__(256) reduce_mixed_kernel(const DevGrid* __rest
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if (lane == 0) {
-    int r, col;  // A-side row, B-side column of element e
-    if (b.transpose_out) { col = (int)(e / b.m); r = (int)(e % b.m); }
-    else { r = (int)(e / b.n); col = (int)(e % b.n); }
+    const int r = (int)(e / b.n), col = (int)(e % b.n);
     const double* rc = rowc + grids[b.grid].rc_off;
-    double ca;
-    if (b.a_mode == 1) {
-      const short2 pr = pairs[b.pair_off + r];
-      ca = rc[b.a_row + pr.x] * rc[b.a_row + pr.y];
-    } else {
-      ca = rc[b.a_row + r] * (b.a_w >= 0 ? rc[b.a_w] : 1.0);
-    }
-    const double cb = rc[b.b_row + col] * (b.b_w >= 0 ? rc[b.b_w] : 1.0);
+    const short2 qa = rows[b.a_off + r], qb = rows[b.b_off + col];
+    const double ca = rc[qa.x] * (qa.y >= 0 ? rc[qa.y] : 1.0);
+    const double cb = rc[qb.x] * (qb.y >= 0 ? rc[qb.y] : 1.0);
     res[b.res_off + e] = s * ca * cb;
   }
 }
@@ -785,7 +775,7 @@ cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const
 size_t ws_smem_bytes() { return sizeof(ws::Smem) + 1024; }
 
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                               int n_ctas, const short2* pairs, const float* ops, float2* part, int* status,
+                               int n_ctas, const short2* rows, const float* ops, float2* part, int* status,
                                cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
   static bool attr_set = false;
@@ -795,17 +785,17 @@ cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, con
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  contract_ws_kernel<<<n_ctas, ws::kThreads, bytes, s>>>(grids, blocks, items, n_items, pairs, ops, part, status);
+  contract_ws_kernel<<<n_ctas, ws::kThreads, bytes, s>>>(grids, blocks, items, n_items, rows, ops, part, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
-                                int64_t n_elems, const short2* pairs, const double* rowc, const float2* part,
+                                int64_t n_elems, const short2* rows, const double* rowc, const float2* part,
                                 double* res, cudaStream_t s) {
   if (n_elems == 0) return cudaSuccess;
   const int64_t threads = n_elems * 32;
   reduce_mixed_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(grids, blocks, n_blocks, elem_begin, n_elems,
-                                                                         pairs, rowc, part, res);
+                                                                         rows, rowc, part, res);
   return cudaGetLastError();
 }
 
