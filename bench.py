@@ -41,9 +41,15 @@ def parse():
     ap.add_argument("--impl", default="psq", choices=["psq", "reference"])
     ap.add_argument("--workload", default="triatomic_oh2")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=3, help="steps of the plain FP64 path timed beside")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the step benchmark")
+    ap.add_argument("--rates", default="20,100", help="serving: Poisson arrival rates (jobs/s)")
+    ap.add_argument("--jobs", type=int, default=24, help="serving: jobs per rate")
+    ap.add_argument("--baseline-jobs", type=int, default=6, help="serving: jobs timed on the per-job FP64 path")
     return ap.parse_args()
 
 
@@ -176,12 +182,86 @@ def recorded_traffic(kernel, workload, precision):
     return None
 
 
+# ------------------------------------------------------------------------------ serving
+
+def serve_main(args):
+    """Poisson stream of random molecules (2..9 atoms, Z in {1,6,7,8}, DZ/TZ/QZ-sized bases,
+    config-2 grids) through the continuous-batching server (mixed precision), against the
+    same jobs run one by one on the plain FP64 path."""
+    import threading
+    import numpy as np
+    import torch
+    import synth
+    from paper_2510_15204_gb300 import build as B
+    B.build()
+    import paper_2510_15204_gb300 as P
+    torch.cuda.set_device(0)
+    ctx = P.Context(0)
+    mask = P.ALL
+    res = {"metric": "serve p50/p99 latency and throughput", "unit": "s", "higher_is_better": False,
+           "data": "synthetic", "n_gpus": 1, "rates": []}
+    arena_bytes = int(torch.cuda.mem_get_info()[0] * 0.6)
+    server = P.Server(ctx, arena_bytes=arena_bytes, max_inflight=6)
+    for rate in [float(x) for x in args.rates.split(",")]:
+        stream = synth.serving_stream(seed=args.seed, rate=rate, n_jobs=args.jobs)
+        jobs = [P.Job.from_synth(ctx, j, P.MIXED) for _, j in stream]
+        outs = [{k: torch.empty(sh, dtype=torch.float64).pin_memory() for k, sh in J.out_shapes(mask).items()}
+                for J in jobs]
+        for J in jobs:
+            J.workspace_bytes(mask)  # plan up front: planning is host work, not serving latency
+        work = sum(J.stats(mask)["contractions"] for J in jobs)
+        tickets = [None] * len(jobs)
+        t0 = time.perf_counter()
+
+        def feeder():
+            for i, (t_arr, _) in enumerate(stream):
+                d = t0 + t_arr - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = server.submit(jobs[i], mask, outs[i])
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        lat = [server.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        res["rates"].append({"rate_per_s": rate, "jobs": len(jobs), "p50_s": float(np.percentile(lat, 50)),
+                             "p99_s": float(np.percentile(lat, 99)), "throughput_jobs_per_s": len(jobs) / wall,
+                             "contractions_per_s": work / wall, "precision": "mixed"})
+    server.close()
+    # per-job plain FP64 launches, one after another, same arrival times (first jobs of the stream)
+    stream = synth.serving_stream(seed=args.seed, rate=float(args.rates.split(",")[0]), n_jobs=args.baseline_jobs)
+    jobs = [P.Job.from_synth(ctx, j, P.FP64) for _, j in stream]
+    lat, busy_until = [], 0.0
+    work = sum(J.stats(mask)["contractions"] for J in jobs)
+    t_gpu = 0.0
+    for (t_arr, _), J in zip(stream, jobs):
+        ws, out = J.alloc(mask)
+        host = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in out.items()}
+        t1 = time.perf_counter()
+        J.compute_host(mask, ws, out, host)
+        dt = time.perf_counter() - t1
+        t_gpu += dt
+        start = max(t_arr, busy_until)  # a single FIFO server of per-job launches
+        busy_until = start + dt
+        lat.append(busy_until - t_arr)
+        del ws, out
+        torch.cuda.empty_cache()
+    res["fp64_per_job"] = {"jobs": len(jobs), "p50_s": float(np.percentile(lat, 50)),
+                           "p99_s": float(np.percentile(lat, 99)), "contractions_per_s": work / t_gpu,
+                           "note": "same stream's first jobs, one launch sequence per job, FIFO"}
+    print(json.dumps(res))
+    return 0
+
+
 # ------------------------------------------------------------------------------ GPU arm
 
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.serve:
+        return serve_main(args)
     rank, world, local = dist_env()
     import torch
     import synth
@@ -228,6 +308,41 @@ def main():
         dist.barrier()
     value = world * st["contractions"] * args.steps / (ms / 1e3)
 
+    # the same steps replayed from the job's captured CUDA graph
+    graph = None
+    if not args.no_graph:
+        with torch.cuda.stream(stream):
+            J.compute_graph(mask, ws, out, stream)
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for _ in range(args.steps):
+                J.compute_graph(mask, ws, out, stream)
+            g1.record(stream)
+            torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / args.steps
+        graph = {"ms_per_step": gms, "value": st["contractions"] / (gms / 1e3)}
+
+    # the plain FP64 path on the same job ("vs plain FP64"), a few steps
+    plain = None
+    if prec == P.MIXED and args.fp64_steps > 0:
+        J64 = P.Job.from_synth(ctx, job, P.FP64)
+        ws64, out64 = J64.alloc(mask)
+        with torch.cuda.stream(stream):
+            J64.compute(mask, ws64, out64, stream)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.fp64_steps):
+                J64.compute(mask, ws64, out64, stream)
+            f1.record(stream)
+            torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / args.fp64_steps
+        plain = {"value": st["contractions"] / (fms / 1e3), "ms_per_step": fms, "steps": args.fp64_steps,
+                 "speedup_of_mixed": fms / (ms / args.steps)}
+        del ws64, out64, J64
+        torch.cuda.empty_cache()
+
     # end to end through the C ABI with host buffers (tables up, matrices down, every step)
     host = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in out.items()}
     with torch.cuda.stream(stream):
@@ -267,7 +382,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == P.FP64 else "f32+bf16x3",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == P.FP64 else "f32 values, bf16 8-bit slices, f32/f64 sums",
         "data": "synthetic",
         "config": {"workload": args.workload, "seed": args.seed, "precision": args.precision,
                    "n_bf": J.n_bf, "n_aux": J.n_aux, "grids": st["grids"], "points": st["points"],
@@ -277,6 +393,8 @@ def main():
         "roofline": roof,
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "graph": graph,
+        "plain_fp64": plain,
         "gpu_launches": st["launches"] * args.steps,
         "clocks": clk,
     }

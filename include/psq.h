@@ -106,6 +106,13 @@ psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_
 psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes,
                        double* d_out[5], void* stream);
 
+/* psq_compute through a CUDA graph: the first call for a (mask, workspace, outputs) triple
+ * plans the job, captures its launch sequence on `stream` (which must not be the legacy
+ * default stream) and instantiates it; every call then launches that graph.  Graphs are
+ * owned by the job and freed with it. */
+psq_status psq_compute_graph(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes,
+                             double* d_out[5], void* stream);
+
 /* psq_compute followed by device-to-host copies of the requested classes into h_out[0..4]
  * (page-locked memory recommended) and a synchronisation of the stream. */
 psq_status psq_compute_host(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes,
@@ -159,6 +166,28 @@ psq_status psq_job_grid_points(psq_job* job, int g, void* d_workspace, size_t ws
  * holds rows x n_points doubles; *rows receives the row count. */
 psq_status psq_job_grid_functions(psq_job* job, int g, int kind, void* d_workspace,
                                   size_t ws_bytes, double* d_out, int* rows, void* stream);
+
+/* Serving: a request loop for jobs of different sizes arriving over time (continuous
+ * batching).  The server owns max_inflight streams and a worker thread; device memory comes
+ * from the caller's arena (d_arena, arena_bytes, 256-byte aligned), first-fit.  A submitted
+ * job waits until its workspace and outputs fit in the arena and a stream is free; waiting
+ * jobs are admitted in submission order, except that a later job that fits runs before an
+ * earlier one that does not (backfilling).  Admitted jobs run concurrently, each on its own
+ * stream, and their requested matrices are copied into h_out[0..4] (host buffers, page-locked
+ * recommended, laid out as psq_compute's outputs).  submit plans the job on the calling
+ * thread (psq_job_workspace) and returns a ticket; PSQ_ERR_OOM if the job can never fit.
+ * poll reports whether the ticket is done and its latency so far (submit to completion);
+ * wait blocks up to timeout_s seconds.  A job's status (e.g. PSQ_ERR_TIMEOUT) is returned by
+ * poll/wait once it is done.  A job must not be destroyed while it has unfinished tickets.
+ * destroy waits for the running jobs and frees the server's streams. */
+typedef struct psq_server psq_server;
+psq_status psq_server_create(psq_context* ctx, void* d_arena, size_t arena_bytes, int max_inflight,
+                             psq_server** out);
+psq_status psq_server_submit(psq_server* server, psq_job* job, unsigned mask, double* h_out[5],
+                             uint64_t* ticket);
+psq_status psq_server_poll(psq_server* server, uint64_t ticket, int* done, double* latency_s);
+psq_status psq_server_wait(psq_server* server, uint64_t ticket, double timeout_s);
+psq_status psq_server_destroy(psq_server* server);
 
 /* Thread-local message describing the calling thread's last error. */
 const char* psq_last_error(void);

@@ -57,6 +57,7 @@ SIGNATURES = [
                            ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     ("psq_compute", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP]),
     ("psq_compute_host", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
+    ("psq_compute_graph", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP]),
     ("psq_job_grid_info", _I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                ctypes.POINTER(ctypes.c_int64)]),
     ("psq_job_grid_points", _I, [_VP, _I, _VP, _SZ, _VP, _VP]),
@@ -66,6 +67,11 @@ SIGNATURES = [
     ("psq_profile_read", _I, [_VP, _PD, ctypes.POINTER(_I)]),
     ("psq_check", _I, [_VP, _U, _VP, _VP]),
     ("psq_compute_noalloc", _I, [_VP, _U, ctypes.POINTER(_VP), _VP]),
+    ("psq_server_create", _I, [_VP, _VP, _SZ, _I, ctypes.POINTER(_VP)]),
+    ("psq_server_submit", _I, [_VP, _VP, _U, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_uint64)]),
+    ("psq_server_poll", _I, [_VP, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    ("psq_server_wait", _I, [_VP, ctypes.c_uint64, _D]),
+    ("psq_server_destroy", _I, [_VP]),
     ("psq_last_error", ctypes.c_char_p, []),
 ]
 
@@ -200,6 +206,15 @@ class Job:
                                  _stream_ptr(stream)))
         return out
 
+    def compute_graph(self, mask, ws, out, stream):
+        """compute() through the job's captured CUDA graph (stream must not be the default)."""
+        ptrs = (ctypes.c_void_p * 5)()
+        for i, k in enumerate(CLASSES):
+            ptrs[i] = out[k].data_ptr() if k in out else None
+        _check(lib().psq_compute_graph(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), ws.numel(), ptrs,
+                                       _stream_ptr(stream)))
+        return out
+
     def compute_noalloc(self, mask, out, stream=None):
         """psq_compute_noalloc: the library's fixed device scratch instead of a workspace;
         mask must have been planned (workspace_bytes(mask)) first."""
@@ -274,3 +289,47 @@ class Job:
                                             ctypes.c_void_p(out.data_ptr()), ctypes.byref(rows),
                                             _stream_ptr(stream)))
         return out[: rows.value]
+
+
+class Server:
+    """Continuous-batching request loop over one device arena (psq_server_*)."""
+
+    def __init__(self, ctx: Context, arena_bytes: int, max_inflight: int = 4):
+        import torch
+        self.ctx = ctx
+        self.arena = torch.empty(arena_bytes, dtype=torch.uint8, device=torch.device("cuda", ctx.device))
+        h = ctypes.c_void_p()
+        _check(lib().psq_server_create(ctx.handle, ctypes.c_void_p(self.arena.data_ptr()), arena_bytes,
+                                       max_inflight, ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, job: Job, mask, host_out) -> int:
+        """host_out: dict class -> pinned CPU float64 tensor of the output shape."""
+        ptrs = (ctypes.c_void_p * 5)()
+        for i, k in enumerate(CLASSES):
+            ptrs[i] = host_out[k].data_ptr() if k in host_out else None
+        t = ctypes.c_uint64()
+        _check(lib().psq_server_submit(self.handle, job.handle, mask, ptrs, ctypes.byref(t)))
+        self._keep[t.value] = (job, host_out)
+        return t.value
+
+    def poll(self, ticket):
+        d, lat = ctypes.c_int(), ctypes.c_double()
+        _check(lib().psq_server_poll(self.handle, ticket, ctypes.byref(d), ctypes.byref(lat)))
+        return bool(d.value), lat.value
+
+    def wait(self, ticket, timeout_s=600.0):
+        _check(lib().psq_server_wait(self.handle, ticket, timeout_s))
+        return self.poll(ticket)[1]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().psq_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

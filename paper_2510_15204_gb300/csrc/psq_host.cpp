@@ -168,11 +168,27 @@ struct psq_job {
   // launch timing: events recorded on the compute stream, read back on request
   struct ProfRec { int kind; cudaEvent_t ev; };
   bool prof_on = false;
+  bool capturing = false;
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> ev_free;
+  // instantiated CUDA graphs of the launch sequence, per (mask, workspace, outputs)
+  struct GraphKey {
+    unsigned mask;
+    void* ws;
+    double* out[5];
+    bool operator<(const GraphKey& o) const {
+      if (mask != o.mask) return mask < o.mask;
+      if (ws != o.ws) return ws < o.ws;
+      for (int c = 0; c < 5; ++c)
+        if (out[c] != o.out[c]) return out[c] < o.out[c];
+      return false;
+    }
+  };
+  std::map<GraphKey, cudaGraphExec_t> graphs;
   ~psq_job() {
     for (auto& r : prof) cudaEventDestroy(r.ev);
     for (auto e : ev_free) cudaEventDestroy(e);
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
   }
 };
 
@@ -845,7 +861,7 @@ psq_status get_plan(psq_job* j, unsigned mask, Plan** out) {
 
 // Records a timing event before a launch of `kind` (kind -1 closes a psq_compute call).
 cudaError_t mark(psq_job* j, int kind, cudaStream_t s) {
-  if (!j->prof_on || j->prof.size() >= (1u << 20)) return cudaSuccess;
+  if (!j->prof_on || j->capturing || j->prof.size() >= (1u << 20)) return cudaSuccess;
   cudaEvent_t e;
   if (!j->ev_free.empty()) {
     e = j->ev_free.back();
@@ -910,6 +926,7 @@ psq_status psq_context_create(int device, psq_context** out) {
     }
   upload_gl_tables(x, w, klm);
   upload_mixed_tables(x, w, klm);
+  CUDA_TRY(prepare_kernels());
   CUDA_TRY(cudaGetLastError());
   int sms = 0;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
@@ -1078,6 +1095,14 @@ psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws
 
 psq_status psq::set_error(psq_status s, const char* msg) { return fail(s, "%s", msg); }
 
+int psq::context_device(const psq_context* ctx) { return ctx ? ctx->device : -1; }
+
+size_t psq::status_offset(psq_job* job, unsigned mask) {
+  std::lock_guard<std::mutex> lk(job->mu);
+  auto it = job->plans.find(mask);
+  return it == job->plans.end() ? 0 : it->second->o_status;
+}
+
 psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
                            void* stream, bool plan_must_exist) {
   if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
@@ -1154,6 +1179,48 @@ psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_
 }
 
 extern "C" {
+
+psq_status psq_compute_graph(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
+                             void* stream) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  if (job->ctx->device < 0) return fail(PSQ_ERR_ARG, "the job's context has no device (planning only)");
+  if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
+  if (mask == 0) return PSQ_OK;
+  if (!d_out) return fail(PSQ_ERR_ARG, "d_out is NULL");
+  psq_job::GraphKey key{};
+  key.mask = mask;
+  key.ws = d_workspace;
+  for (int c = 0; c < 5; ++c) key.out[c] = ((mask >> c) & 1) ? d_out[c] : nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto it = job->graphs.find(key);
+  if (it == job->graphs.end()) {
+    // plan first (host work and the page-locked staging buffer stay out of the capture)
+    Plan* P = nullptr;
+    psq_status st = get_plan(job, mask, &P);
+    if (st != PSQ_OK) return st;
+    if (!d_workspace || ws_bytes < P->ws_bytes)
+      return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->ws_bytes);
+    if (!s) return fail(PSQ_ERR_ARG, "graph capture needs a non-default stream");
+    CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    job->capturing = true;
+    st = psq::compute_on(job, mask, d_workspace, ws_bytes, d_out, stream, true);
+    job->capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+    if (st != PSQ_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ec != cudaSuccess) return fail(PSQ_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(PSQ_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    it = job->graphs.emplace(key, exec).first;
+  }
+  CUDA_TRY(cudaGraphLaunch(it->second, s));
+  return PSQ_OK;
+}
 
 psq_status psq_profile_enable(psq_job* job, int on) {
   if (!job) return fail(PSQ_ERR_ARG, "job is NULL");

@@ -136,6 +136,7 @@ cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, con
 cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const float2* xi, float* ops,
                               cudaStream_t s);
 size_t ws_smem_bytes();
+cudaError_t prepare_kernels();  // per-device kernel attributes (context creation)
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
                                int n_ctas, const short2* rows, const float* ops, float2* part, int* status,
                                cudaStream_t s);
@@ -148,4 +149,6 @@ cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, in
 psq_status compute_on(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
                       void* stream, bool plan_must_exist);
 psq_status set_error(psq_status s, const char* msg);
+int context_device(const psq_context* ctx);           // -1 for a planning-only context
+size_t status_offset(psq_job* job, unsigned mask);     // workspace offset of the status word
 }  // namespace psq

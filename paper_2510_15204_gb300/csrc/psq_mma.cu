@@ -455,6 +455,10 @@ __device__ __forceinline__ bool named_sync_producers_or(bool pred) {
   return r != 0;
 }
 
+__device__ __forceinline__ void prefetch_l2(const float* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar) : "memory");
 }
@@ -595,6 +599,19 @@ __global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevG
       }
       for (int64_t ch = ch0; ch < ch1; ++ch, ++c) {
         const int st = c & 1;
+        // pull this thread's rows of the chunk after next into L2 while this one is built
+        if (ch + 2 < ch1) {
+          const int64_t kp = (ch + 2) * kChunk + 32 * ah;
+          if (avalid) {
+            ws::prefetch_l2(asrc + kp);
+            if (amul) ws::prefetch_l2(amul + kp);
+          }
+          if (btask && bvalid) {
+            const int64_t kb = (ch + 2) * kChunk + 32 * (tid & 1);
+            ws::prefetch_l2(bsrc + kb);
+            if (bmul) ws::prefetch_l2(bmul + kb);
+          }
+        }
         bool ok = true;
         if (c >= 2) ok = mbar_wait(smem_u32(&sm.freed[st]), ((c - 2) >> 1) & 1);
         if (!ok) atomicExch(status, 2);
@@ -774,17 +791,15 @@ cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const
 
 size_t ws_smem_bytes() { return sizeof(ws::Smem) + 1024; }
 
+cudaError_t prepare_kernels() {
+  return cudaFuncSetAttribute(contract_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes());
+}
+
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
                                int n_ctas, const short2* rows, const float* ops, float2* part, int* status,
                                cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  static bool attr_set = false;
   const size_t bytes = ws_smem_bytes();
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(contract_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
   contract_ws_kernel<<<n_ctas, ws::kThreads, bytes, s>>>(grids, blocks, items, n_items, rows, ops, part, status);
   return cudaGetLastError();
 }
