@@ -369,9 +369,12 @@ def main():
             roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
         else:
+            # the tensor pipe's roofline counts the MMAs it issues: 10 slice products per useful tile
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-            roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12, "peak": peaks["bf16_tflops"],
-                    "unit": "TFLOP/s", "peak_source": "measured bf16 burst"}
+            roof = {"bound": "tensor", "achieved": st["issued_flops"] / per_launch_s / 1e12,
+                    "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "peak_source": "measured bf16 burst",
+                    "counts": "issued bf16 MMA FLOPs (8-bit slice products, padded tiles)",
+                    "useful_tflops": flops / per_launch_s / 1e12}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
     roof["kernel"] = kind

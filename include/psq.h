@@ -98,6 +98,14 @@ psq_status psq_job_workspace(const psq_job* job, unsigned mask, size_t* bytes);
 psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_t* n_points,
                          double* contractions, int* launches);
 
+/* Floating-point operations the contraction kernel issues in one psq_compute for mask (the
+ * measure a tensor-pipe roofline counts; no paper counterpart).  PSQ_MIXED: every tensor-core
+ * MMA of the 8-bit slice products, a 128-row tile padded to the 16-column multiple, 10 slice
+ * products per 64-point chunk, each M x N x K MMA counting 2MNK.  PSQ_FP64: 2 x rows x cols x
+ * points summed over the computed blocks.  Errors: PSQ_ERR_ARG for NULL pointers or unknown
+ * mask bits. */
+psq_status psq_job_issued_flops(const psq_job* job, unsigned mask, double* flops);
+
 /* Computes the classes in mask, asynchronously on `stream` (a cudaStream_t; NULL = legacy
  * default stream).  d_out[0..4] are device buffers for S, T, V (n_bf*n_bf doubles each,
  * row-major), J2 (n_aux*n_aux) and J3 (n_aux*n_bf*n_bf, [P][i][j]); entries for classes
@@ -124,7 +132,7 @@ psq_status psq_job_io_bytes(const psq_job* job, unsigned mask, size_t* h2d, size
 
 /* Launch timing.  While enabled, psq_compute records a CUDA event on its stream before each
  * step: 0 table upload, 1 grid + function evaluation, 2 contraction, 3 chunk reduction,
- * 4 assembly (all classes).  psq_profile_read waits for the recorded events, returns the
+ * 4 assembly (all classes), 5 operand packing (PSQ_MIXED only).  psq_profile_read waits for the recorded events, returns the
  * summed milliseconds and counts per step kind (8 slots) and clears the record. */
 psq_status psq_profile_enable(psq_job* job, int on);
 psq_status psq_profile_read(psq_job* job, double ms[8], int counts[8]);

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("psq_job_workspace", _I, [_VP, _U, ctypes.POINTER(_SZ)]),
     ("psq_job_stats", _I, [_VP, _U, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    ("psq_job_issued_flops", _I, [_VP, _U, ctypes.POINTER(ctypes.c_double)]),
     ("psq_compute", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP]),
     ("psq_compute_host", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("psq_compute_graph", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP]),
@@ -177,7 +178,10 @@ class Job:
         g, p, c, n = ctypes.c_int(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_int()
         _check(lib().psq_job_stats(self.handle, mask, ctypes.byref(g), ctypes.byref(p), ctypes.byref(c),
                                    ctypes.byref(n)))
-        return {"grids": g.value, "points": p.value, "contractions": c.value, "launches": n.value}
+        f = ctypes.c_double()
+        _check(lib().psq_job_issued_flops(self.handle, mask, ctypes.byref(f)))
+        return {"grids": g.value, "points": p.value, "contractions": c.value, "launches": n.value,
+                "issued_flops": f.value}
 
     def out_shapes(self, mask=ALL):
         nb, na = self.n_bf, self.n_aux
@@ -244,7 +248,7 @@ class Job:
         _check(lib().psq_job_io_bytes(self.handle, mask, ctypes.byref(h), ctypes.byref(d)))
         return h.value, d.value
 
-    PROFILE_KINDS = ("upload", "eval", "contract", "reduce", "assemble", "k5", "k6", "k7")
+    PROFILE_KINDS = ("upload", "eval", "contract", "reduce", "assemble", "pack", "k6", "k7")
 
     def profile(self, on: bool):
         _check(lib().psq_profile_enable(self.handle, 1 if on else 0))

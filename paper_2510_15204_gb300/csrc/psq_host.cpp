@@ -55,6 +55,7 @@ psq_status fail(psq_status s, const char* fmt, ...) {
 
 constexpr double kOnAxisTol = 1e-10;  // a third centre this close (x a) to the axis is on it
 constexpr int kPointsPerBlock = 128;
+constexpr int64_t kMaxChunkPoints = 32768;  // FP64 path: points per sequential partial sum
 constexpr int kSmCount = 152;
 
 // Gauss-Legendre rule by Newton's method on P_q (Bonnet recurrence); nodes ascending.
@@ -135,7 +136,10 @@ struct Plan {
   bool mixed = false;
   std::vector<MmaBlock> mblocks;
   std::vector<GemmItem> mitems;
-  size_t o_mb = 0, o_mi = 0, nodes_off = 0, o_xi = 0, o_rc = 0;
+  std::vector<Panel> panels;
+  std::vector<PairTile> ptiles;
+  int64_t n_pack_jobs = 0, pack_bytes = 0;
+  size_t o_mb = 0, o_mi = 0, o_pn = 0, o_pt = 0, nodes_off = 0, o_xi = 0, o_rc = 0, pack_off = 0;
   std::vector<float2> xi;    // per grid: (hi, lo) scale turning rho into x = zeta r, per shell
   std::vector<double> rowc;  // per grid: FP64 constant of every operand row
   int64_t n_nodes = 0;
@@ -144,6 +148,7 @@ struct Plan {
   bool pinned = false;
   int64_t n_points = 0;
   double contractions = 0;
+  double issued_flops = 0;
   int launches = 0;
   ~Plan() {
     if (staging && pinned) cudaFreeHost(staging);
@@ -384,7 +389,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     }
     g.row_W = rows;
     rows += 4;
-    g.ld = (int64_t)align_up((size_t)g.K, 64);
+    g.ld = (int64_t)align_up((size_t)g.K, 128);
     g.op_off = ops;
     ops += (int64_t)rows * g.ld;
     P.n_points += g.K;
@@ -471,7 +476,11 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     for (size_t bi = 0; bi < P.gblocks.size(); ++bi) {
       GemmBlock& b = P.gblocks[bi];
       const int64_t K = P.grids[b.grid].K;
-      b.n_chunks = (int)std::max<int64_t>(1, std::min<int64_t>(cglob, (K + 2047) / 2048));
+      // at most kMaxChunkPoints per sequential partial sum (bounded rounding growth), and
+      // more chunks where the grid has too few tiles to fill the GPU
+      b.n_chunks = (int)std::max<int64_t>((K + kMaxChunkPoints - 1) / kMaxChunkPoints,
+                                          std::min<int64_t>(cglob, (K + 2047) / 2048));
+      b.n_chunks = std::max(1, b.n_chunks);
       b.part_off = part;
       part += (int64_t)b.n_chunks * b.m * b.n;
       const int tm = (b.m + kTile - 1) / kTile, tn = (b.n + kTile - 1) / kTile;
@@ -483,6 +492,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     P.elem_begin[0] = 0;
     for (size_t bi = 0; bi < P.gblocks.size(); ++bi)
       P.elem_begin[bi + 1] = P.elem_begin[bi] + (int64_t)P.gblocks[bi].m * P.gblocks[bi].n;
+    for (const GemmBlock& b : P.gblocks) P.issued_flops += 2.0 * b.m * b.n * (double)P.grids[b.grid].K;
     for (int X = 0; X < nat; ++X) {
       for (int Y = 0; Y < nat; ++Y) {
         for (int c = 0; c < 4; ++c) P.src_ptr[c][X * nat + Y] = (int)P.src[c].size();
@@ -514,63 +524,147 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       }
     }
   } else {
-    // Tensor-core path: per grid one pair block (all local pairs chi_i chi_j against the
-    // weighted aux potentials and the plain weights w, w/r_A, w/r_B or w/r_C, giving J3, S
-    // and V together), one kinetic block and one (P|Q) block.
-    struct GridBlocks { int pair = -1, kin = -1, j2 = -1, colS = -1, colVA = -1, colVB = -1, colVC = -1; };
+    // Tensor-core path.  Per pair grid: the weighted aux potentials U w form the A panel of
+    // the 3-index block (against the pair products chi_i chi_j, formed in the kernel: J3) and
+    // of the (P|Q) block (against the aux functions: J2); the weighted operand rows
+    // [w lap chi | w chi | w/r_A chi | w/r_B chi] form the A panel of the 2-index block
+    // against the basis functions (T, S, V).  Per refined grid: [U_C w | w/r_C] against the
+    // A x B pair products (J3 and V).
+    struct GridBlocks { int pair = -1, kin = -1, j2 = -1, rowT = -1, rowS = -1, rowVA = -1, rowVB = -1, rowVC = -1; };
     std::vector<GridBlocks> gbk(P.grids.size());
-    auto add_mblock = [&](int g, int m, int n, int a_off, int b_off) {
+    auto add_panel = [&](int g, int rows_off, int nrows, int tr) {
+      const DevGrid& G = P.grids[g];
+      Panel pn{};
+      pn.grid = g; pn.rows_off = rows_off; pn.nrows = nrows; pn.tr = tr;
+      pn.n_tiles = (nrows + tr - 1) / tr;
+      pn.nch = (int)((G.K + 63) / 64);
+      pn.nwin = (pn.nch + 1) / 2;
+      pn.pack_off = P.pack_bytes;
+      P.pack_bytes += (int64_t)align_up((size_t)nrows * pn.nch * 4 * 128, 256);
+      pn.exp_off = P.pack_bytes;
+      P.pack_bytes += (int64_t)align_up((size_t)pn.n_tiles * pn.nwin * tr * 4, 256);
+      pn.job_begin = P.n_pack_jobs;
+      P.n_pack_jobs += (int64_t)pn.n_tiles * pn.nwin;
+      P.panels.push_back(pn);
+      return (int)P.panels.size() - 1;
+    };
+    auto add_mblock = [&](int g, int m, int n, int a_off, int b_off, int a_panel, int b_panel, int ptile_off,
+                          int n_btiles) {
       MmaBlock b{};
-      b.grid = g; b.m = m; b.n = n; b.a_off = a_off; b.b_off = b_off; b.res_off = res;
+      b.grid = g; b.m = m; b.n = n; b.a_off = a_off; b.b_off = b_off;
+      b.a_panel = a_panel; b.b_panel = b_panel; b.ptile_off = ptile_off; b.n_btiles = n_btiles;
+      b.res_off = res;
       res += (int64_t)m * n;
       P.mblocks.push_back(b);
       return (int)P.mblocks.size() - 1;
+    };
+    // Pair tiles of a 3-index block: the pairs (result column, row x, row y) visited in 8 x 8
+    // blocks of (i, j), cut into tiles of <= 64 columns and <= kPairTileRows distinct rows.
+    struct PairRef { int col, x, y; };
+    auto add_pair_tiles = [&](const std::vector<PairRef>& pl) {
+      const int first = (int)P.ptiles.size();
+      PairTile t{};
+      auto flush = [&]() {
+        if (t.ncols > 0) P.ptiles.push_back(t);
+        t = PairTile{};
+      };
+      auto slot = [&](int row) {
+        for (int k = 0; k < t.nrows; ++k)
+          if (t.rows[k] == row) return k;
+        return -1;
+      };
+      for (const PairRef& pr : pl) {
+        const int need = (slot(pr.x) < 0) + (pr.y != pr.x && slot(pr.y) < 0);
+        if (t.ncols == 64 || t.nrows + need > kPairTileRows) flush();
+        int sx = slot(pr.x);
+        if (sx < 0) { sx = t.nrows; t.rows[t.nrows++] = (short)pr.x; }
+        int sy = slot(pr.y);
+        if (sy < 0) { sy = t.nrows; t.rows[t.nrows++] = (short)pr.y; }
+        t.dx[t.ncols] = (unsigned char)sx;
+        t.dy[t.ncols] = (unsigned char)sy;
+        t.col[t.ncols] = pr.col;
+        ++t.ncols;
+      }
+      flush();
+      return std::make_pair(first, (int)P.ptiles.size() - first);
     };
     for (size_t gi = 0; gi < P.grids.size(); ++gi) {
       const DevGrid& g = P.grids[gi];
       const int nl = g.nFA + g.nFB, W = g.row_W;
       GridBlocks& gb = gbk[gi];
       if (g.C < 0) {
-        const bool j3 = (mask & PSQ_J3) && g.nG > 0;
-        if (nl > 0 && (j3 || (mask & (PSQ_S | PSQ_V)))) {
-          const int a_off = (int)P.pairs.size();
+        const bool j3 = (mask & PSQ_J3) && g.nG > 0 && nl > 0;
+        const bool j2 = (mask & PSQ_J2) && g.nG > 0;
+        int pu = -1, u_off = -1;
+        if (j3 || j2) {
+          u_off = (int)P.pairs.size();
+          for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
+          pu = add_panel((int)gi, u_off, g.nG, 128);
+        }
+        if (j3) {
+          // all local pairs i <= j, result columns in packed row-major order
+          const int b_off = (int)P.pairs.size();
           for (int i = 0; i < nl; ++i)
             for (int jj = i; jj < nl; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + jj));
-          const int b_off = (int)P.pairs.size();
-          if (j3)
-            for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
-          if (mask & PSQ_S) { gb.colS = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W, -1)); }
-          if (mask & PSQ_V) {
-            gb.colVA = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W + 1, -1));
-            gb.colVB = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W + 2, -1));
+          std::vector<PairRef> pl;
+          for (int ib = 0; ib < nl; ib += 8)
+            for (int jb = ib; jb < nl; jb += 8)
+              for (int i = ib; i < std::min(nl, ib + 8); ++i)
+                for (int jj = std::max(i, jb); jj < std::min(nl, jb + 8); ++jj)
+                  pl.push_back(PairRef{i * nl - i * (i - 1) / 2 + (jj - i), g.row_F + i, g.row_F + jj});
+          const auto tl = add_pair_tiles(pl);
+          gb.pair = add_mblock((int)gi, g.nG, nl * (nl + 1) / 2, u_off, b_off, pu, -1, tl.first, tl.second);
+        }
+        if ((mask & (PSQ_S | PSQ_T | PSQ_V)) && nl > 0) {
+          // 2-index block: [w lap chi | w chi | w/r_A chi | w/r_B chi] against chi
+          const int a_off = (int)P.pairs.size();
+          if (mask & PSQ_T) {
+            gb.rowT = 0;
+            for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_L + i, W));
           }
-          gb.pair = add_mblock((int)gi, nl * (nl + 1) / 2, (int)P.pairs.size() - b_off, a_off, b_off);
-        }
-        if ((mask & PSQ_T) && nl > 0) {
-          const int a_off = (int)P.pairs.size();
+          if (mask & PSQ_S) {
+            gb.rowS = (int)P.pairs.size() - a_off;
+            for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_F + i, W));
+          }
+          if (mask & PSQ_V) {
+            gb.rowVA = (int)P.pairs.size() - a_off;
+            for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_F + i, W + 1));
+            gb.rowVB = (int)P.pairs.size() - a_off;
+            for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_F + i, W + 2));
+          }
+          const int na_rows = (int)P.pairs.size() - a_off;
+          const int pk = add_panel((int)gi, a_off, na_rows, 128);
+          const int b_off = (int)P.pairs.size();
           for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_F + i, -1));
-          const int b_off = (int)P.pairs.size();
-          for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_L + i, W));
-          gb.kin = add_mblock((int)gi, nl, nl, a_off, b_off);
+          const int pf = add_panel((int)gi, b_off, nl, 64);
+          gb.kin = add_mblock((int)gi, na_rows, nl, a_off, b_off, pk, pf, -1, 0);
         }
-        if ((mask & PSQ_J2) && g.nG > 0) {
-          const int a_off = (int)P.pairs.size();
-          for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_G + q, -1));
+        if (j2) {
           const int b_off = (int)P.pairs.size();
-          for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
-          gb.j2 = add_mblock((int)gi, g.nG, g.nG, a_off, b_off);
+          for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_G + q, -1));
+          const int pg = add_panel((int)gi, b_off, g.nG, 64);
+          gb.j2 = add_mblock((int)gi, g.nG, g.nG, u_off, b_off, pu, pg, -1, 0);
         }
       } else if (g.nFA > 0 && g.nFB > 0) {
         const bool j3 = (mask & PSQ_J3) && g.nG > 0;
         if (j3 || (mask & PSQ_V)) {
           const int a_off = (int)P.pairs.size();
-          for (int i = 0; i < g.nFA; ++i)
-            for (int jj = 0; jj < g.nFB; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + g.nFA + jj));
-          const int b_off = (int)P.pairs.size();
           if (j3)
             for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
-          if (mask & PSQ_V) { gb.colVC = (int)P.pairs.size() - b_off; P.pairs.push_back(make_short2(W + 3, -1)); }
-          gb.pair = add_mblock((int)gi, g.nFA * g.nFB, (int)P.pairs.size() - b_off, a_off, b_off);
+          if (mask & PSQ_V) { gb.rowVC = (int)P.pairs.size() - a_off; P.pairs.push_back(make_short2(W + 3, -1)); }
+          const int na_rows = (int)P.pairs.size() - a_off;
+          const int pc = add_panel((int)gi, a_off, na_rows, 128);
+          const int b_off = (int)P.pairs.size();
+          for (int i = 0; i < g.nFA; ++i)
+            for (int jj = 0; jj < g.nFB; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + g.nFA + jj));
+          std::vector<PairRef> pl;
+          for (int ib = 0; ib < g.nFA; ib += 8)
+            for (int jb = 0; jb < g.nFB; jb += 8)
+              for (int i = ib; i < std::min(g.nFA, ib + 8); ++i)
+                for (int jj = jb; jj < std::min(g.nFB, jb + 8); ++jj)
+                  pl.push_back(PairRef{i * g.nFB + jj, g.row_F + i, g.row_F + g.nFA + jj});
+          const auto tl = add_pair_tiles(pl);
+          gb.pair = add_mblock((int)gi, na_rows, g.nFA * g.nFB, a_off, b_off, pc, -1, tl.first, tl.second);
         }
       }
     }
@@ -583,25 +677,32 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
         const int gi = gidx[grid_for(j, X, Y, X)];
         const DevGrid& G = P.grids[gi];
         const GridBlocks& gb = gbk[gi];
-        const int nl = G.nFA + G.nFB, oX = local_off(G, X), oY = local_off(G, Y);
-        if ((mask & PSQ_S) && gb.pair >= 0)
-          P.src[0].push_back(SrcEntry{blk(gb.pair).res_off, blk(gb.pair).n, oX, oY, 0, gb.colS, 1, nl, 0, 1.0});
-        if ((mask & PSQ_T) && gb.kin >= 0)
-          P.src[1].push_back(SrcEntry{blk(gb.kin).res_off, nl, oX, oY, oY, oX, 0, 0, 0, 1.0});
+        const int oX = local_off(G, X), oY = local_off(G, Y);
+        if ((mask & PSQ_S) && gb.kin >= 0) {
+          const MmaBlock& k = blk(gb.kin);
+          P.src[0].push_back(SrcEntry{k.res_off, k.n, gb.rowS + oX, oY, gb.rowS + oY, oX, 0, 0, 0, 1.0});
+        }
+        if ((mask & PSQ_T) && gb.kin >= 0) {
+          const MmaBlock& k = blk(gb.kin);
+          P.src[1].push_back(SrcEntry{k.res_off, k.n, gb.rowT + oX, oY, gb.rowT + oY, oX, 0, 0, 0, 1.0});
+        }
         if (mask & PSQ_V) {
           for (int C = 0; C < nat; ++C) {
             const GridKey k = grid_for(j, X, Y, C);
             const int hv = gidx[k];
             const DevGrid& H = P.grids[hv];
             const GridBlocks& hb = gbk[hv];
-            if (hb.pair < 0) continue;
             const double z = -(double)j->atoms[C].Z;
             if (k.C >= 0) {
-              P.src[2].push_back(SrcEntry{blk(hb.pair).res_off, blk(hb.pair).n, 0, 0, 0, hb.colVC, 2, H.nFB, 0, z});
+              if (hb.pair < 0) continue;
+              const MmaBlock& pb = blk(hb.pair);
+              P.src[2].push_back(SrcEntry{pb.res_off, 1, 0, 0, 0, hb.rowVC, 2, H.nFB, pb.n, z});
             } else {
-              const int col = C == H.A ? hb.colVA : hb.colVB;
-              P.src[2].push_back(SrcEntry{blk(hb.pair).res_off, blk(hb.pair).n, local_off(H, X), local_off(H, Y), 0,
-                                          col, 1, H.nFA + H.nFB, 0, z});
+              if (hb.kin < 0) continue;
+              const MmaBlock& kb = blk(hb.kin);
+              const int row = C == H.A ? hb.rowVA : hb.rowVB;
+              const int hX = local_off(H, X), hY = local_off(H, Y);
+              P.src[2].push_back(SrcEntry{kb.res_off, kb.n, row + hX, hY, row + hY, hX, 0, 0, 0, z});
             }
           }
         }
@@ -623,24 +724,27 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
             if (gb.pair < 0) continue;
             const MmaBlock& b = blk(gb.pair);
             if (k.C >= 0)
-              J3at(X, Y, W) = J3Src{b.res_off, b.n, 1, 0, G.nFB, 0, 0};
+              J3at(X, Y, W) = J3Src{b.res_off, 1, b.n, 0, G.nFB, 0, 0};
             else
-              J3at(X, Y, W) = J3Src{b.res_off + aux_off(G, X), b.n, 1, 1, G.nFA + G.nFB, local_off(G, Y),
-                                    local_off(G, W)};
+              J3at(X, Y, W) = J3Src{b.res_off + (int64_t)aux_off(G, X) * b.n, 1, b.n, 1, G.nFA + G.nFB,
+                                    local_off(G, Y), local_off(G, W)};
           }
     }
-    // work items: 128 x 64 tiles of every block, its point range cut for load balance
+    // work items: 128-row x 64-column tiles of every block, its windows cut for load balance
     int64_t mtiles = 0;
-    for (auto& mb : P.mblocks) mtiles += (int64_t)((mb.m + 127) / 128) * ((mb.n + 63) / 64);
+    for (auto& mb : P.mblocks)
+      mtiles += (int64_t)((mb.m + 127) / 128) * (mb.b_panel >= 0 ? (mb.n + 63) / 64 : mb.n_btiles);
     const int64_t want = 4LL * kSmCount;
     const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi) {
       MmaBlock& mb = P.mblocks[bi];
-      const int64_t nch = (P.grids[mb.grid].K + 63) / 64;
-      mb.n_ranges = (int)std::max<int64_t>(1, std::min<int64_t>(cr, (nch + 15) / 16));
+      const int64_t nwin = ((P.grids[mb.grid].K + 63) / 64 + 1) / 2;
+      const int64_t r0 = std::max<int64_t>(1, std::min<int64_t>(cr, (nwin + 7) / 8));
+      mb.win_per = (int)((nwin + r0 - 1) / r0);
+      mb.n_ranges = (int)((nwin + mb.win_per - 1) / mb.win_per);
       mb.part_off = part;
       part += (int64_t)mb.n_ranges * mb.m * mb.n;
-      const int tm = (mb.m + 127) / 128, tn = (mb.n + 63) / 64;
+      const int tm = (mb.m + 127) / 128, tn = mb.b_panel >= 0 ? (mb.n + 63) / 64 : mb.n_btiles;
       for (int c = 0; c < mb.n_ranges; ++c)
         for (int x = 0; x < tm; ++x)
           for (int y = 0; y < tn; ++y) P.mitems.push_back(GemmItem{(int)bi, x, y, c});
@@ -648,11 +752,18 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     auto item_chunks = [&](const GemmItem& it) {
       const MmaBlock& mb = P.mblocks[it.block];
       const int64_t nch = (P.grids[mb.grid].K + 63) / 64;
-      const int64_t per = (nch + mb.n_ranges - 1) / mb.n_ranges;
-      return std::max<int64_t>(0, std::min<int64_t>(nch, per * (it.chunk + 1)) - per * it.chunk);
+      const int64_t c0 = 2LL * it.chunk * mb.win_per;
+      return std::max<int64_t>(0, std::min<int64_t>(nch, c0 + 2LL * mb.win_per) - c0);
     };
     std::stable_sort(P.mitems.begin(), P.mitems.end(),
                      [&](const GemmItem& x, const GemmItem& y) { return item_chunks(x) > item_chunks(y); });
+    // issued tensor work: per 64-point chunk of an item, 10 slice products of a 128 x ntp x 64 tile
+    for (const GemmItem& it : P.mitems) {
+      const MmaBlock& mb = P.mblocks[it.block];
+      const int nt = mb.b_panel >= 0 ? std::min(64, mb.n - it.tn * 64) : P.ptiles[mb.ptile_off + it.tn].ncols;
+      const int ntp = (nt + 15) & ~15;
+      P.issued_flops += (double)item_chunks(it) * 10.0 * 2.0 * 128.0 * ntp * 64.0;
+    }
     P.elem_begin.resize(P.mblocks.size() + 1);
     P.elem_begin[0] = 0;
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi)
@@ -756,7 +867,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   }
   int nclasses = 0;
   for (int c = 0; c < 5; ++c) nclasses += (mask >> c) & 1;
-  P.launches = P.grids.empty() ? 0 : (P.mixed ? 4 : 3) + nclasses;
+  P.launches = P.grids.empty() ? 0 : (P.mixed ? 5 : 3) + nclasses;
   // table layout
   size_t off = 0;
   auto sec = [&](size_t bytes) {
@@ -785,6 +896,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   P.o_j3 = sec(sizeof(J3Src) * P.j3.size());
   P.o_mb = sec(sizeof(MmaBlock) * P.mblocks.size());
   P.o_mi = sec(sizeof(GemmItem) * P.mitems.size());
+  P.o_pn = sec(sizeof(Panel) * P.panels.size());
+  P.o_pt = sec(sizeof(PairTile) * P.ptiles.size());
   P.o_status = sec(sizeof(int) * 4);
   P.o_xi = sec(sizeof(float2) * P.xi.size());
   P.o_rc = sec(sizeof(double) * P.rowc.size());
@@ -793,6 +906,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   off = align_up(off + sizeof(NodeEntry) * (size_t)P.n_nodes, 256);
   P.ops_off = off;
   off = align_up(off + esize * (size_t)ops, 256);
+  P.pack_off = off;
+  off = align_up(off + (size_t)P.pack_bytes, 256);
   P.part_off = off;
   off = align_up(off + sizeof(double) * (size_t)part, 256);
   P.res_off = off;
@@ -838,6 +953,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   put(P.o_j3, P.j3.data(), sizeof(J3Src) * P.j3.size());
   put(P.o_mb, P.mblocks.data(), sizeof(MmaBlock) * P.mblocks.size());
   put(P.o_mi, P.mitems.data(), sizeof(GemmItem) * P.mitems.size());
+  put(P.o_pn, P.panels.data(), sizeof(Panel) * P.panels.size());
+  put(P.o_pt, P.ptiles.data(), sizeof(PairTile) * P.ptiles.size());
   put(P.o_xi, P.xi.data(), sizeof(float2) * P.xi.size());
   put(P.o_rc, P.rowc.data(), sizeof(double) * P.rowc.size());
   return PSQ_OK;
@@ -1086,6 +1203,16 @@ psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_
   return PSQ_OK;
 }
 
+psq_status psq_job_issued_flops(const psq_job* job, unsigned mask, double* flops) {
+  if (!job || !flops) return fail(PSQ_ERR_ARG, "job or flops is NULL");
+  if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
+  Plan* P = nullptr;
+  psq_status st = get_plan(const_cast<psq_job*>(job), mask, &P);
+  if (st != PSQ_OK) return st;
+  *flops = P->issued_flops;
+  return PSQ_OK;
+}
+
 psq_status psq_compute(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
                        void* stream) {
   return psq::compute_on(job, mask, d_workspace, ws_bytes, d_out, stream, false);
@@ -1139,10 +1266,15 @@ psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_
     CUDA_TRY(mark(job, 1, s));
     CUDA_TRY(launch_nodes(t.grids, (int)P->grids.size(), P->max_node_entries, t.edges, nodes, s));
     CUDA_TRY(launch_eval_mixed(t, nodes, (const float2*)(ws + P->o_xi), ops, s));
+    CUDA_TRY(mark(job, 5, s));
+    uint8_t* packed = (uint8_t*)(ws + P->pack_off);
+    CUDA_TRY(launch_pack(t.grids, (const Panel*)(ws + P->o_pn), (int)P->panels.size(), P->n_pack_jobs, t.pairs, ops,
+                         packed, s));
     CUDA_TRY(mark(job, 2, s));
     const int n_items = (int)P->mitems.size();
     CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi), n_items,
-                                std::min(n_items, job->ctx->sm_count), t.pairs, ops, (float2*)part,
+                                std::min(n_items, job->ctx->sm_count), (const Panel*)(ws + P->o_pn),
+                                (const PairTile*)(ws + P->o_pt), ops, packed, (float2*)part,
                                 (int*)(ws + P->o_status), s));
     CUDA_TRY(mark(job, 3, s));
     CUDA_TRY(launch_reduce_mixed(t.grids, (const MmaBlock*)(ws + P->o_mb), (int)P->mblocks.size(), t.elem_begin,

@@ -57,13 +57,48 @@ struct NodeEntry { double v, s, c, h2, g2, w; };
 // A contraction block of the tensor-core path: R[r][c] = sum_p A_r(p) B_c(p), row-major
 // m x n, where every operand row is one of the grid's operand rows times an optional second
 // one: A_r = src[a.x] * src[a.y] (a = rows[a_off + r], y = -1: no factor), B_c likewise from
-// rows[b_off + c].  This covers pair products chi_i chi_j and weighted rows w chi, w V^P.
+// rows[b_off + c].  A always comes from a packed panel (a_panel); B from a packed panel
+// (b_panel >= 0) or, for the 3-index operand chi_i chi_j, is formed in shared memory from
+// the staged basis rows of the pair tiles [ptile_off, ptile_off + n_btiles).
 struct MmaBlock {
   int grid;
   int m, n;
   int a_off, b_off;
-  int n_ranges;
+  int n_ranges, win_per;  // point range split into n_ranges of win_per 128-point windows
+  int a_panel, b_panel;
+  int ptile_off, n_btiles;
   int64_t res_off, part_off;
+};
+
+// A packed operand panel: nrows operand rows (rows[rows_off ...]) of one grid in tiles of tr
+// rows (128 for the A side of a tile, 64 for B); tile t holds rt = min(tr, nrows - t*tr) rows.
+// Every value is split into four BF16 planes of 8-bit integers under a power-of-two scale
+// per row and 128-point window (exponent e: value = 2^(e-7) (s0 + s1/256 + s2/256^2 +
+// s3/256^3)).  The planes of tile t, 64-point chunk c start at pack_off + t*nch*4*tr*128 +
+// c*4*rt*128 bytes, plane k rt*128 bytes after plane k-1, each exactly as the tcgen05
+// shared-memory operand wants it: 128-byte rows (64 points), the eight 16-byte groups of row
+// r XOR-swizzled by r % 8.  Rows past rt are not stored (their products only reach result
+// rows or columns that are never read).  The exponents of tile t, window w are tr ints at
+// exp_off + (t*nwin + w)*tr*4 bytes; a zero row (or padding row) has exponent kZeroExp.
+struct Panel {
+  int grid;
+  int rows_off, nrows;
+  int tr, n_tiles;
+  int nch, nwin;
+  int64_t pack_off, exp_off;
+  int64_t job_begin;  // first (tile, window) packing job of this panel in a prefix over panels
+};
+constexpr int kZeroExp = -100000;
+
+// The formed B operand of one 64-column tile of a 3-index block: column c is the product of
+// the staged basis rows dx[c] and dy[c] (indices into rows[], grid operand rows) and lands
+// in column col[c] of the block's result.
+constexpr int kPairTileRows = 24;
+struct PairTile {
+  int ncols, nrows;
+  short rows[kPairTileRows];
+  unsigned char dx[64], dy[64];
+  int col[64];
 };
 
 // One output block of a contraction (eq 9): out[r][c] = sum_p A_r(p) d(p) B_c(p), where
@@ -87,11 +122,11 @@ struct GemmItem { int block, tm, tn, chunk; };
 // Two-index element (a on X, b on Y, local indices la, lb) from block M = res + off:
 //   mode 0: M[(rX+la)*ld + cY+lb], averaged with its mirror M[(rY+lb)*ld + cX+la] where the
 //           class is symmetrised;
-//   mode 1: M[p*ld + cX], p = packed index of the local pair (rX+la, cY+lb) over nloc;
-//   mode 2: M[p*ld + cX], p = la*nloc + lb (a rectangular pair list).
+//   mode 1: M[p*ld + cX*cs], p = packed index of the local pair (rX+la, cY+lb) over nloc;
+//   mode 2: M[p*ld + cX*cs], p = la*nloc + lb (a rectangular pair list).
 struct SrcEntry {
   int64_t off;
-  int ld, rX, cY, rY, cX, mode, nloc, pad;
+  int ld, rX, cY, rY, cX, mode, nloc, cs;
   double z;
 };
 // Three-index element (P on X, i on Y, j on W; Y <= W): res[off + p*s_pair + lP*s_aux] with
@@ -137,9 +172,11 @@ cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const
                               cudaStream_t s);
 size_t ws_smem_bytes();
 cudaError_t prepare_kernels();  // per-device kernel attributes (context creation)
+cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
+                        const float* ops, uint8_t* packed, cudaStream_t s);
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                               int n_ctas, const short2* rows, const float* ops, float2* part, int* status,
-                               cudaStream_t s);
+                               int n_ctas, const Panel* panels, const PairTile* ptiles, const float* ops,
+                               const uint8_t* packed, float2* part, int* status, cudaStream_t s);
 cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
                                 int64_t n_elems, const short2* rows, const double* rowc, const float2* part,
                                 double* res, cudaStream_t s);

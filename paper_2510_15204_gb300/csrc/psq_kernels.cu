@@ -312,15 +312,22 @@ __global__ void __launch_bounds__(256) contract_fp64_kernel(LaunchTables t, cons
       Bs[pp][r] = bv;
     }
     __syncthreads();
+    // sub-sums of the tile's 32 points first, so that small outer-region terms are not
+    // absorbed one by one into a large running sum
+    double s00 = 0, s01 = 0, s10 = 0, s11 = 0;
 #pragma unroll 8
     for (int pp = 0; pp < kTile; ++pp) {
       const double a0 = As[pp][2 * tm], a1 = As[pp][2 * tm + 1];
       const double b0 = Bs[pp][2 * tn], b1 = Bs[pp][2 * tn + 1];
-      acc00 = fma(a0, b0, acc00);
-      acc01 = fma(a0, b1, acc01);
-      acc10 = fma(a1, b0, acc10);
-      acc11 = fma(a1, b1, acc11);
+      s00 = fma(a0, b0, s00);
+      s01 = fma(a0, b1, s01);
+      s10 = fma(a1, b0, s10);
+      s11 = fma(a1, b1, s11);
     }
+    acc00 += s00;
+    acc01 += s01;
+    acc10 += s10;
+    acc11 += s11;
     __syncthreads();
   }
   double* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n;
@@ -394,7 +401,7 @@ __global__ void assemble2_kernel(int cls, int nat, int nfn, const int* __restric
       } else {
         p = (int64_t)la * s.nloc + lb;
       }
-      v += s.z * M[p * s.ld + s.cX];
+      v += s.z * M[p * s.ld + (int64_t)s.cX * s.cs];
     }
   }
   out[idx] = v;

@@ -337,7 +337,6 @@ constexpr int kM = 128;         // tile rows (pairs, or the bigger side of a 2-i
 constexpr int kTileN = 64;       // tile columns
 constexpr int kChunk = 64;      // points per scale window and smem stage (128 bytes of BF16)
 constexpr int kSlices = 4;      // 8-bit integer slices per operand value (orders 0..3 kept)
-constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -372,19 +371,37 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the phase of the given parity; gives up (false) after kWaitNs nanoseconds, or
+// early once *abort (if given) is set by another role of the CTA.
+constexpr uint64_t kWaitNs = 4000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const int* abort = nullptr) {
+  if (mbar_try(mbar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(mbar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (abort && *(volatile const int*)abort) return false;
+      if (global_ns() - t0 > kWaitNs) return false;
+    }
   }
-  return false;
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
@@ -396,6 +413,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
       : "r"(taddr));
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -411,150 +437,243 @@ __device__ __forceinline__ float pow2f(int k) {
 
 }  // namespace mma
 
-// ------------------------------------------------------------------ warp-specialised version
+// ------------------------------------------------------------------ operand packing
 //
-// One persistent CTA per SM (512 threads).  Warps 0-7 produce: for each 64-point chunk they
-// build the A tile (128 rows) and the B tile (<= 64 rows) as four integer slices in one of two
-// shared-memory stages, two threads per row (32 points each); lane 0 of warp 0 then issues
-// the chunk's 40 MMAs into one of two TMEM accumulator sets and commits them to full[stage].
-// Warps 8-15 fold: they wait full[stage], read the four order accumulators of their lane
-// quadrant and column half, add the chunk into double-float registers and arrive at
-// free[stage], which lets the producers reuse the stage and the TMEM set.  A CTA's point
-// range ends with a write of (hi, lo) pairs; the FP64 reduction applies the row constants.
+// Every operand row that a tile reads as a whole (weighted aux potentials, weighted kinetic
+// operands, basis and aux functions) is sliced once per job into the tcgen05 shared-memory
+// image by pack_kernel; the contraction then moves it with bulk copies.  Only the 3-index
+// operand chi_i chi_j, whose rows are products of two basis rows, is formed inside the
+// contraction, from basis rows staged in shared memory.
+
+namespace mma {
+
+// Eight values, already scaled into (-128, 128), as four planes of 8-bit integers in BF16:
+// plane k holds the nearest integer of what planes 0..k-1 left, times 256^k.  w[k] is the
+// 16-byte group of plane k.
+__device__ __forceinline__ void slice8(const float* v, float sc, uint4* w) {
+  uint32_t o[kSlices][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float r0 = v[2 * q] * sc, r1 = v[2 * q + 1] * sc;
+#pragma unroll
+    for (int k = 0; k < kSlices; ++k) {
+      const float a0 = rintf(r0), a1 = rintf(r1);
+      const __nv_bfloat162 p = __floats2bfloat162_rn(a0, a1);
+      o[k][q] = *reinterpret_cast<const uint32_t*>(&p);
+      r0 = (r0 - a0) * 256.0f;
+      r1 = (r1 - a1) * 256.0f;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kSlices; ++k) w[k] = make_uint4(o[k][0], o[k][1], o[k][2], o[k][3]);
+}
+
+// Exponent e with max < 2^e (frexp), or kZeroExp for a row that is zero (or below 2^-110).
+__device__ __forceinline__ int row_exponent(float mx) {
+  int e = 0;
+  if (mx > 0.0f) frexpf(mx, &e);
+  return (!(mx > 0.0f) || e < -110) ? kZeroExp : e;
+}
+
+// Byte offset of 16-byte group j of row r in a 128-byte-row swizzled operand tile.
+__device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)r * 128u + ((uint32_t)(j ^ (r & 7)) << 4); }
+
+}  // namespace mma
+
+// One CTA per (panel, tile, 128-point window); thread (r, h) packs row r of the tile for
+// chunk 2w + h.  The two threads of a row share the window's scale.
+__global__ void __launch_bounds__(256) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
+                                                   int n_panels, const short2* __restrict__ rows,
+                                                   const float* __restrict__ ops, uint8_t* __restrict__ packed) {
+  using namespace mma;
+  const int64_t job = blockIdx.x;
+  int lo = 0, hi = n_panels;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (panels[mid].job_begin <= job) lo = mid; else hi = mid;
+  }
+  const Panel pn = panels[lo];
+  const int64_t lj = job - pn.job_begin;
+  const int t = (int)(lj / pn.nwin), w = (int)(lj % pn.nwin);
+  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+  if (r >= pn.tr) return;  // whole warps
+  const DevGrid& g = grids[pn.grid];
+  const int c = 2 * w + h;
+  const int row = t * pn.tr + r;
+  const float* src = nullptr;
+  const float* mul = nullptr;
+  if (row < pn.nrows && c < pn.nch) {
+    const short2 q = rows[pn.rows_off + row];
+    src = ops + g.op_off + (int64_t)q.x * g.ld + 64 * (int64_t)c;
+    if (q.y >= 0) mul = ops + g.op_off + (int64_t)q.y * g.ld + 64 * (int64_t)c;
+  }
+  const int64_t left = g.K - 64 * (int64_t)c;
+  float v[64];
+  if (src && left >= 64) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const float4* m4 = reinterpret_cast<const float4*>(mul);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      float4 a = __ldg(s4 + i);
+      if (mul) {
+        const float4 b = __ldg(m4 + i);
+        a.x *= b.x; a.y *= b.y; a.z *= b.z; a.w *= b.w;
+      }
+      v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = (src && i < left) ? src[i] * (mul ? mul[i] : 1.0f) : 0.0f;
+  }
+  float mx = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 64; ++i) mx = fmaxf(mx, fabsf(v[i]));
+  const unsigned pair_mask = 3u << ((threadIdx.x & 31) & ~1u);
+  mx = fmaxf(mx, __shfl_xor_sync(pair_mask, mx, 1));
+  const int e = row_exponent(mx);
+  if (h == 0)
+    *reinterpret_cast<int*>(packed + pn.exp_off + (((int64_t)t * pn.nwin + w) * pn.tr + r) * 4) = e;
+  const int rt = min(pn.tr, pn.nrows - t * pn.tr);  // rows stored for this tile
+  if (c >= pn.nch || r >= rt) return;
+  const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
+  uint8_t* dst = packed + pn.pack_off + (int64_t)t * pn.nch * (4 * pn.tr * 128) + (int64_t)c * (4 * rt * 128);
+  const int plane = rt * 128;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    uint4 wv[kSlices];
+    slice8(v + 8 * j, sc, wv);
+#pragma unroll
+    for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(r, j)) = wv[k];
+  }
+}
+
+// ------------------------------------------------------------------ warp-specialised contraction
+//
+// One persistent CTA per SM, 512 threads, working through tiles (128 A rows x <= 64 B
+// columns x a range of 128-point windows):
+//   warp 4       loader: bulk copies of the packed A tile (and packed B tile) of every 64-point
+//                chunk into a two-stage ring, and of the staged basis rows of formed B tiles
+//                (one copy per row and window);
+//   warps 0-3    producers: for a formed B, column c of the tile = product of two staged rows,
+//                sliced under one scale per column and window into the chunk's B stage (for a
+//                packed B they only pass each chunk on);
+//   warp 5       MMA issue: per chunk 4 K-steps x 10 slice products (orders 0..3) into the
+//                window's TMEM accumulator set (4 orders x 64 columns; two sets);
+//   warps 8-15   fold: per window, the four order sums of their TMEM lane quadrant and column
+//                half, scaled by the window's row and column exponents, into double-float
+//                registers; at the end of the tile, (hi, lo) partials to global memory.
+// All integer sums stay below 2^23 (|slice| <= 128, <= 4 products per order, 128 points), so
+// the FP32 accumulators hold them exactly.  Every wait is bounded; a timeout sets *status and
+// the CTA's abort flag, and each role leaves its loops at its next wait.
 
 namespace ws {
 
-constexpr int kProducers = 256;
-constexpr int kEpi = 256;
-constexpr int kThreads = kProducers + kEpi;
-constexpr int kStages = 2;
+constexpr int kThreads = 512;
+constexpr int kLoadWarp = 4, kMmaWarp = 5, kFoldWarp0 = 8;
+constexpr int kRawStride = 132;  // floats per staged row: 128 points + 4 (bank spread)
 
 struct Smem {
-  alignas(1024) uint8_t a[kStages][mma::kSlices][mma::kM * 128];
-  alignas(1024) uint8_t b[kStages][mma::kSlices][mma::kTileN * 128];
-  int ea[kStages][mma::kM];
-  int eb[kStages][mma::kTileN];
-  alignas(8) uint64_t full[kStages];
-  alignas(8) uint64_t freed[kStages];
+  alignas(1024) uint8_t a[2][mma::kSlices][mma::kM * 128];
+  alignas(1024) uint8_t b[2][mma::kSlices][mma::kTileN * 128];
+  alignas(16) float raw[2][kPairTileRows][kRawStride];
+  int eb[2][mma::kTileN];
+  int ebw[8][mma::kTileN];  // fold warp k: the column exponents of the current window
+  alignas(8) uint64_t a_full[2], b_ready[2], stage_free[2], tmem_full[2], tmem_free[2], raw_full[2], raw_free[2];
+  uint64_t drain;
   uint32_t tmem_base;
   int abort;
 };
 
-// Barrier of the 256 producer threads that also ORs a predicate over them, so every producer
-// takes the same decision from it.
-__device__ __forceinline__ bool named_sync_producers_or(bool pred) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, %2, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}\n"
-      : "=r"(r)
-      : "r"((uint32_t)pred), "n"(kProducers)
-      : "memory");
-  return r != 0;
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mma::smem_u32(b)), "r"(count));
 }
 
-__device__ __forceinline__ void prefetch_l2(const float* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mma::smem_u32(b))
+               : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(mbar) : "memory");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   mma::smem_u32(b)),
+               "r"(bytes)
+               : "memory");
 }
 
-// 32 values of half a row -> four slices (bytes [64h, 64h+64) of the row in each slice).
-__device__ __forceinline__ void slice_half(const float* v, float sc, int row, int h, uint8_t* const* sl) {
-  const uint32_t rowoff = (uint32_t)row * 128u;
-  const uint32_t sw = (uint32_t)(row & 7);
-#pragma unroll
-  for (int cc = 0; cc < 4; ++cc) {
-    const int c = 4 * h + cc;  // 16-byte chunk index within the 128-byte row
-    uint32_t w[mma::kSlices][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float r0 = v[8 * cc + 2 * q] * sc, r1 = v[8 * cc + 2 * q + 1] * sc;
-#pragma unroll
-      for (int k = 0; k < mma::kSlices; ++k) {
-        const float a0 = rintf(r0), a1 = rintf(r1);
-        const __nv_bfloat162 p = __floats2bfloat162_rn(a0, a1);
-        w[k][q] = *reinterpret_cast<const uint32_t*>(&p);
-        r0 = (r0 - a0) * 256.0f;
-        r1 = (r1 - a1) * 256.0f;
-      }
-    }
-    const uint32_t off = rowoff + (((uint32_t)c ^ sw) << 4);
-#pragma unroll
-    for (int k = 0; k < mma::kSlices; ++k)
-      *reinterpret_cast<uint4*>(sl[k] + off) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
-  }
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completing
+// on mbarrier b.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   mma::smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(mma::smem_u32(b))
+               : "memory");
 }
 
-__device__ __forceinline__ void load32(const float* __restrict__ src, const float* __restrict__ mul, int64_t k0,
-                                       int64_t K, float* v) {
-  if (k0 + 32 <= K) {
-    const float4* s4 = reinterpret_cast<const float4*>(src + k0);
-    const float4* m4 = reinterpret_cast<const float4*>(mul + k0);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float4 q = __ldg(s4 + i);
-      if (mul) {
-        const float4 m = __ldg(m4 + i);
-        q.x *= m.x; q.y *= m.y; q.z *= m.z; q.w *= m.w;
-      }
-      v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = (k0 + i < K) ? src[k0 + i] * (mul ? mul[k0 + i] : 1.0f) : 0.0f;
-  }
+__device__ __forceinline__ bool wait(uint64_t* b, uint32_t parity, const int* abort = nullptr) {
+  return mma::mbar_wait(mma::smem_u32(b), parity, abort);
 }
 
-// One producer task: half h of operand row `row` of the tile (values from the grid's FP32
-// rows), sliced into stage `st`.  Returns nothing; the row's exponent goes to *e_out (h == 0).
-__device__ __forceinline__ void produce_half(const float* src, const float* mul, int64_t k0, int64_t K, bool valid,
-                                             int row, int h, uint8_t* const* sl, int* e_out) {
-  float v[32];
-  if (valid) {
-    load32(src, mul, k0 + 32 * h, K, v);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = 0.0f;
-  }
-  float mx = 0.0f;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[i]));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  int e = 0;
-  if (mx > 0.0f) frexpf(mx, &e);
-  const bool zero = !(mx > 0.0f) || e < -110;
-  slice_half(v, zero ? 0.0f : mma::pow2f(7 - e), row, h, sl);
-  if (h == 0) *e_out = zero ? -100000 : e;
+// What every role needs to know about an item.
+struct Geo {
+  const MmaBlock* blk;
+  int64_t K;
+  int nch, nwin, w0, w1;
+  int nt, ntp;      // B columns of the tile and their multiple of 16
+  bool formed;
+  const PairTile* pt;
+};
+
+__device__ __forceinline__ Geo geo(const GemmItem& it, const MmaBlock* blocks, const DevGrid* grids,
+                                   const PairTile* ptiles) {
+  Geo q;
+  q.blk = blocks + it.block;
+  const MmaBlock& b = *q.blk;
+  q.K = grids[b.grid].K;
+  q.nch = (int)((q.K + 63) / 64);
+  q.nwin = (q.nch + 1) / 2;
+  q.w0 = it.chunk * b.win_per;
+  q.w1 = min(q.nwin, q.w0 + b.win_per);
+  q.formed = b.b_panel < 0;
+  q.pt = q.formed ? ptiles + b.ptile_off + it.tn : nullptr;
+  q.nt = q.formed ? q.pt->ncols : min(mma::kTileN, b.n - it.tn * mma::kTileN);
+  q.ntp = (q.nt + 15) & ~15;
+  return q;
 }
+
+__device__ __forceinline__ void fail(Smem& sm, int* status, int code) {
+  *(volatile int*)&sm.abort = 1;
+  atomicCAS(status, 0, code);  // the first failure's code stays
+}
+
+__device__ __forceinline__ bool aborted(Smem& sm) { return *(volatile int*)&sm.abort != 0; }
 
 }  // namespace ws
 
-__global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevGrid* __restrict__ grids,
-                                                                      const MmaBlock* __restrict__ blocks,
-                                                                      const GemmItem* __restrict__ items, int n_items,
-                                                                      const short2* __restrict__ rows,
-                                                                      const float* __restrict__ ops,
-                                                                      float2* __restrict__ part,
-                                                                      int* __restrict__ status) {
+__global__ void __launch_bounds__(ws::kThreads, 1)
+    contract_ws_kernel(const DevGrid* __restrict__ grids, const MmaBlock* __restrict__ blocks,
+                       const GemmItem* __restrict__ items, int n_items, const Panel* __restrict__ panels,
+                       const PairTile* __restrict__ ptiles, const float* __restrict__ ops,
+                       const uint8_t* __restrict__ packed, float2* __restrict__ part, int* __restrict__ status) {
   using namespace mma;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   ws::Smem& sm = *reinterpret_cast<ws::Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 8) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == ws::kMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
                  "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < ws::kStages; ++s) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.full[s])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(&sm.freed[s])));
+    for (int s = 0; s < 2; ++s) {
+      ws::mbar_init(&sm.a_full[s], 1);
+      ws::mbar_init(&sm.b_ready[s], 4);
+      ws::mbar_init(&sm.stage_free[s], 1);
+      ws::mbar_init(&sm.tmem_full[s], 1);
+      ws::mbar_init(&sm.tmem_free[s], 8);
+      ws::mbar_init(&sm.raw_full[s], 1);
+      ws::mbar_init(&sm.raw_free[s], 4);
     }
+    ws::mbar_init(&sm.drain, 1);
     sm.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -562,166 +681,287 @@ __global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevG
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm.tmem_base;
-  uint32_t c = 0;  // chunks of this CTA so far (stage = c & 1, TMEM set = c & 1)
+  uint32_t c = 0, w = 0, rw = 0;  // chunks, windows and formed windows of this CTA so far
 
-  if (tid < ws::kProducers) {
-    // ------------------------------------------------------------ producers (+ MMA issue)
-    bool stop = false;
-    for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+  constexpr unsigned kFull = 0xffffffffu;
+  if (warp == ws::kLoadWarp) {
+    // ------------------------------------------------------------------ loader
+    bool run = true;                 // warp-uniform
+    int last_a = -1, last_raw = -1;  // last issued chunk / formed window (for the drain)
+    for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
       const GemmItem it = items[ii];
-      const MmaBlock b = blocks[it.block];
+      const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
+      const MmaBlock& b = *q.blk;
       const DevGrid& g = grids[b.grid];
-      const float* base = ops + g.op_off;
-      const int64_t ld = g.ld, K = g.K;
-      const int nt = min(kTileN, b.n - it.tn * kTileN), ntp = (nt + 15) & ~15;
-      const int r0 = it.tm * kM, c0 = it.tn * kTileN;
-      const int64_t nchunk = (K + kChunk - 1) / kChunk;
-      const int64_t per = (nchunk + b.n_ranges - 1) / b.n_ranges;
-      const int64_t ch0 = (int64_t)it.chunk * per, ch1 = min(nchunk, ch0 + per);
-      const uint32_t idesc = make_idesc(ntp);
-      // this thread's A task: row tid/2, half tid%2; B task (tid < 2 ntp): column tid/2
-      const int arow = tid >> 1, ah = tid & 1;
-      const int grow = r0 + arow;
-      const bool avalid = grow < b.m;
-      const float *asrc = nullptr, *amul = nullptr;
-      if (avalid) {
-        const short2 q = rows[b.a_off + grow];
-        asrc = base + (int64_t)q.x * ld;
-        amul = q.y >= 0 ? base + (int64_t)q.y * ld : nullptr;
-      }
-      const int brow = tid >> 1;
-      const bool btask = tid < 2 * ntp, bvalid = brow < nt;
-      const float *bsrc = nullptr, *bmul = nullptr;
-      if (bvalid) {
-        const short2 q = rows[b.b_off + c0 + brow];
-        bsrc = base + (int64_t)q.x * ld;
-        bmul = q.y >= 0 ? base + (int64_t)q.y * ld : nullptr;
-      }
-      for (int64_t ch = ch0; ch < ch1; ++ch, ++c) {
-        const int st = c & 1;
-        // pull this thread's rows of the chunk after next into L2 while this one is built
-        if (ch + 2 < ch1) {
-          const int64_t kp = (ch + 2) * kChunk + 32 * ah;
-          if (avalid) {
-            ws::prefetch_l2(asrc + kp);
-            if (amul) ws::prefetch_l2(amul + kp);
+      const Panel& pa = panels[b.a_panel];
+      const Panel* pb = q.formed ? nullptr : panels + b.b_panel;
+      for (int win = q.w0; win < q.w1 && run; ++win, ++w) {
+        const int nck = min(2, q.nch - 2 * win);
+        if (q.formed) {
+          const int rb = rw & 1;
+          const bool ok = rw < 2 || ws::wait(&sm.raw_free[rb], ((rw - 2) >> 1) & 1, &sm.abort);
+          run = __all_sync(kFull, ok && !ws::aborted(sm));
+          if (!run) { ws::fail(sm, status, 4); break; }
+          const int nr = q.pt->nrows;
+          if (lane == 0) ws::mbar_expect_tx(&sm.raw_full[rb], (uint32_t)nr * 512u);
+          __syncwarp();
+          if (lane < nr)
+            ws::bulk_g2s(sm.raw[rb][lane], ops + g.op_off + (int64_t)q.pt->rows[lane] * g.ld + 128 * (int64_t)win,
+                         512u, &sm.raw_full[rb]);
+          last_raw = (int)rw;
+          ++rw;
+        }
+        for (int j = 0; j < nck; ++j, ++c) {
+          const int s = c & 1, ch = 2 * win + j;
+          const bool ok = c < 2 || ws::wait(&sm.stage_free[s], ((c - 2) >> 1) & 1, &sm.abort);
+          run = __all_sync(kFull, ok && !ws::aborted(sm));
+          if (!run) { ws::fail(sm, status, 4); break; }
+          // the stored rows of the tiles, one bulk copy per plane (lanes 0-3: A, 4-7: B)
+          const int ra = min(kM, pa.nrows - it.tm * kM);
+          const int rbw = pb ? min(kTileN, pb->nrows - it.tn * kTileN) : 0;
+          if (lane == 0) ws::mbar_expect_tx(&sm.a_full[s], 4u * 128u * (uint32_t)(ra + rbw));
+          __syncwarp();
+          if (lane < 4) {
+            const uint8_t* src = packed + pa.pack_off + (int64_t)it.tm * pa.nch * (4 * kM * 128) +
+                                 (int64_t)ch * (4 * ra * 128) + (int64_t)lane * ra * 128;
+            ws::bulk_g2s(sm.a[s][lane], src, 128u * (uint32_t)ra, &sm.a_full[s]);
+          } else if (lane < 8 && pb) {
+            const int k = lane - 4;
+            const uint8_t* src = packed + pb->pack_off + (int64_t)it.tn * pb->nch * (4 * kTileN * 128) +
+                                 (int64_t)ch * (4 * rbw * 128) + (int64_t)k * rbw * 128;
+            ws::bulk_g2s(sm.b[s][k], src, 128u * (uint32_t)rbw, &sm.a_full[s]);
           }
-          if (btask && bvalid) {
-            const int64_t kb = (ch + 2) * kChunk + 32 * (tid & 1);
-            ws::prefetch_l2(bsrc + kb);
-            if (bmul) ws::prefetch_l2(bmul + kb);
+          __syncwarp();
+          last_a = (int)c;
+        }
+      }
+    }
+    // drain: nothing may still be copying into shared memory when the CTA exits
+    if (!run) {
+      for (int k = last_a; k >= 0 && k > last_a - 2; --k) ws::wait(&sm.a_full[k & 1], (k >> 1) & 1);
+      for (int k = last_raw; k >= 0 && k > last_raw - 2; --k) ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1);
+    }
+  } else if (warp < 4) {
+    // ------------------------------------------------------------------ producers
+    const int col = tid >> 1, h = tid & 1;
+    const unsigned pair_mask = 3u << ((tid & 31) & ~1u);
+    bool run = true;  // warp-uniform
+    for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
+      const GemmItem it = items[ii];
+      const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
+      if (!q.formed) {
+        // packed B: the loader brings it; b_ready still completes one phase per chunk
+        for (int win = q.w0; win < q.w1 && run; ++win, ++w) {
+          const int nck = min(2, q.nch - 2 * win);
+          for (int j = 0; j < nck; ++j, ++c) {
+            const bool ok = c < 2 || ws::wait(&sm.stage_free[c & 1], ((c - 2) >> 1) & 1, &sm.abort);
+            run = __all_sync(kFull, ok && !ws::aborted(sm));
+            if (!run) { ws::fail(sm, status, 5); break; }
+            if (lane == 0) ws::mbar_arrive(&sm.b_ready[c & 1]);
           }
         }
-        bool ok = true;
-        if (c >= 2) ok = mbar_wait(smem_u32(&sm.freed[st]), ((c - 2) >> 1) & 1);
-        if (!ok) atomicExch(status, 2);
-        const int64_t k0 = ch * kChunk;
-        uint8_t* asl[kSlices] = {sm.a[st][0], sm.a[st][1], sm.a[st][2], sm.a[st][3]};
-        ws::produce_half(asrc, amul, k0, K, avalid, arow, ah, asl, &sm.ea[st][arow]);
-        if (btask) {
-          uint8_t* bsl[kSlices] = {sm.b[st][0], sm.b[st][1], sm.b[st][2], sm.b[st][3]};
-          ws::produce_half(bsrc, bmul, k0, K, bvalid, brow, tid & 1, bsl, &sm.eb[st][brow]);
+        continue;
+      }
+      const bool valid = col < q.nt;
+      const int dx = valid ? q.pt->dx[col] : 0, dy = valid ? q.pt->dy[col] : 0;
+      for (int win = q.w0; win < q.w1 && run; ++win, ++w, ++rw) {
+        const int nck = min(2, q.nch - 2 * win);
+        const int rb = rw & 1, set = w & 1;
+        const uint32_t cc = c + h;  // this thread's chunk
+        bool ok = ws::wait(&sm.raw_full[rb], (rw >> 1) & 1, &sm.abort);
+        if (ok && w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort);
+        if (ok && h < nck && cc >= 2) ok = ws::wait(&sm.stage_free[cc & 1], ((cc - 2) >> 1) & 1, &sm.abort);
+        run = __all_sync(kFull, ok && !ws::aborted(sm));
+        if (!run) { ws::fail(sm, status, 5); break; }
+        const float* rx = sm.raw[rb][dx] + 64 * h;
+        const float* ry = sm.raw[rb][dy] + 64 * h;
+        // points of this thread's chunk that exist (none for a padding column)
+        const int64_t left = valid ? q.K - (128 * (int64_t)win + 64 * h) : 0;
+        float mx = 0.0f;
+        if (h < nck) {
+#pragma unroll
+          for (int i = 0; i < 64; i += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(rx + i);
+            const float4 bq = *reinterpret_cast<const float4*>(ry + i);
+            const float p0 = i + 0 < left ? a.x * bq.x : 0.0f, p1 = i + 1 < left ? a.y * bq.y : 0.0f;
+            const float p2 = i + 2 < left ? a.z * bq.z : 0.0f, p3 = i + 3 < left ? a.w * bq.w : 0.0f;
+            mx = fmaxf(fmaxf(mx, fabsf(p0)), fmaxf(fabsf(p1), fmaxf(fabsf(p2), fabsf(p3))));
+          }
+        }
+        mx = fmaxf(mx, __shfl_xor_sync(pair_mask, mx, 1));
+        const int e = row_exponent(mx);
+        if (h == 0) sm.eb[set][col] = e;
+        if (h < nck) {
+          const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
+          uint8_t* dst = sm.b[cc & 1][0];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u += 4) {
+              const float4 a = *reinterpret_cast<const float4*>(rx + 8 * j + u);
+              const float4 bq = *reinterpret_cast<const float4*>(ry + 8 * j + u);
+              const int i = 8 * j + u;
+              v[u + 0] = i + 0 < left ? a.x * bq.x : 0.0f;
+              v[u + 1] = i + 1 < left ? a.y * bq.y : 0.0f;
+              v[u + 2] = i + 2 < left ? a.z * bq.z : 0.0f;
+              v[u + 3] = i + 3 < left ? a.w * bq.w : 0.0f;
+            }
+            uint4 wv[kSlices];
+            slice8(v, sc, wv);
+#pragma unroll
+            for (int k = 0; k < kSlices; ++k)
+              *reinterpret_cast<uint4*>(dst + k * (kTileN * 128) + swz(col, j)) = wv[k];
+          }
         }
         fence_async_smem();
-        // one decision for all producers: stop if any of them timed out or the fold warps did
-        if (ws::named_sync_producers_or(!ok || *(volatile int*)&sm.abort)) { stop = true; break; }
-        if (tid == 0) {
-          fence_after();
-          const uint32_t tset = tmem + (uint32_t)st * 256u;
+        __syncwarp();
+        if (lane == 0) {
+          ws::mbar_arrive(&sm.b_ready[c & 1]);
+          if (nck == 2) ws::mbar_arrive(&sm.b_ready[(c + 1) & 1]);
+          ws::mbar_arrive(&sm.raw_free[rb]);
+        }
+        c += nck;
+      }
+    }
+  } else if (warp == ws::kMmaWarp) {
+    // ------------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      for (int ii = blockIdx.x; ii < n_items && !ws::aborted(sm); ii += gridDim.x) {
+        const GemmItem it = items[ii];
+        const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
+        const uint32_t idesc = make_idesc(q.ntp);
+        bool ok = true;
+        for (int win = q.w0; win < q.w1 && ok; ++win, ++w) {
+          const int nck = min(2, q.nch - 2 * win);
+          const int set = w & 1;
+          if (w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort);
+          const uint32_t tset = tmem + (uint32_t)set * 256u;
+          for (int j = 0; j < nck && ok; ++j, ++c) {
+            const int s = c & 1;
+            ok = ws::wait(&sm.a_full[s], (c >> 1) & 1, &sm.abort);
+            if (ok) ok = ws::wait(&sm.b_ready[s], (c >> 1) & 1, &sm.abort);
+            if (!ok) break;
+            fence_after();
 #pragma unroll
-          for (int k = 0; k < kChunk / 16; ++k) {
-            const uint32_t ko = 32u * k;
+            for (int k = 0; k < kChunk / 16; ++k) {
+              const uint32_t ko = 32u * k;
 #pragma unroll
-            for (int ord = 0; ord < kSlices; ++ord) {
+              for (int ord = 0; ord < kSlices; ++ord) {
 #pragma unroll
-              for (int i = 0; i <= ord; ++i) {
-                const uint64_t da = make_desc(smem_u32(sm.a[st][i]) + ko);
-                const uint64_t db = make_desc(smem_u32(sm.b[st][ord - i]) + ko);
-                mma_bf16(tset + ord * ntp, da, db, idesc, (k > 0 || i > 0) ? 1u : 0u);
+                for (int i = 0; i <= ord; ++i) {
+                  const uint64_t da = make_desc(smem_u32(sm.a[s][i]) + ko);
+                  const uint64_t db = make_desc(smem_u32(sm.b[s][ord - i]) + ko);
+                  mma_bf16(tset + ord * q.ntp, da, db, idesc, (j > 0 || k > 0 || i > 0) ? 1u : 0u);
+                }
               }
             }
+            mma_commit(smem_u32(&sm.stage_free[s]));
           }
-          mma_commit(smem_u32(&sm.full[st]));
+          if (!ok) { ws::fail(sm, status, 6); break; }
+          mma_commit(smem_u32(&sm.tmem_full[set]));
         }
+        if (!ok) break;
       }
-      if (stop) break;
+      // drain: every issued MMA must be complete before the TMEM is released
+      if (ws::aborted(sm)) {
+        mma_commit(smem_u32(&sm.drain));
+        ws::wait(&sm.drain, 0);
+      }
     }
-  } else {
-    // ------------------------------------------------------------ fold (epilogue) warps
-    const int lane = tid & 31;
-    const int ew = warp - 8;             // 0..7
-    const int quad = warp & 3;           // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;            // column groups g with g % 2 == half
+    __syncwarp();
+  } else if (warp >= ws::kFoldWarp0) {
+    // ------------------------------------------------------------------ fold
+    const int ew = warp - ws::kFoldWarp0;  // 0..7
+    const int quad = warp & 3;             // TMEM lane quadrant this warp may access
+    const int half = ew >> 2;              // 16-column groups gq with gq % 2 == half
     const int row_in_tile = quad * 32 + lane;
-    for (int ii = blockIdx.x; ii < n_items; ii += gridDim.x) {
+    bool run = true;  // warp-uniform
+    for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
       const GemmItem it = items[ii];
-      const MmaBlock b = blocks[it.block];
-      const DevGrid& g = grids[b.grid];
-      const int64_t K = g.K;
-      const int nt = min(kTileN, b.n - it.tn * kTileN), ntp = (nt + 15) & ~15;
-      const int r0 = it.tm * kM, c0 = it.tn * kTileN;
-      const int64_t nchunk = (K + kChunk - 1) / kChunk;
-      const int64_t per = (nchunk + b.n_ranges - 1) / b.n_ranges;
-      const int64_t ch0 = (int64_t)it.chunk * per, ch1 = min(nchunk, ch0 + per);
+      const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
+      const MmaBlock& b = *q.blk;
+      const Panel& pa = panels[b.a_panel];
+      const Panel* pb = q.formed ? nullptr : panels + b.b_panel;
       float H[32], L[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) { H[j] = 0.0f; L[j] = 0.0f; }
-      bool ok = true;
-      for (int64_t ch = ch0; ch < ch1; ++ch, ++c) {
-        const int st = c & 1;
-        ok = mbar_wait(smem_u32(&sm.full[st]), (c >> 1) & 1);
-        if (!ok) { *(volatile int*)&sm.abort = 1; atomicExch(status, 3); break; }
+      for (int win = q.w0; win < q.w1; ++win, ++w) {
+        const int set = w & 1;
+        // the window's exponents: A rows from the packed panel, B columns from the packed
+        // panel (one per lane, for this warp's 32 columns) or from the producers
+        const int ea = __ldg(reinterpret_cast<const int*>(packed + pa.exp_off) +
+                             ((int64_t)it.tm * pa.nwin + win) * kM + row_in_tile);
+        const int my_col = (2 * (lane >> 4) + half) * 16 + (lane & 15);
+        int eb_lane = 0;
+        if (pb)
+          eb_lane = __ldg(reinterpret_cast<const int*>(packed + pb->exp_off) +
+                          ((int64_t)it.tn * pb->nwin + win) * kTileN + my_col);
+        const bool ok = ws::wait(&sm.tmem_full[set], (w >> 1) & 1, &sm.abort);
+        run = __all_sync(kFull, ok && !ws::aborted(sm));
+        if (!run) { ws::fail(sm, status, 7); break; }
         fence_after();
-        const int ea = sm.ea[st][row_in_tile];
-        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)st * 256u;
+        int* ebw = sm.ebw[ew];
+        ebw[my_col] = pb ? eb_lane : sm.eb[set][my_col];
+        __syncwarp();
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * 256u;
 #pragma unroll
         for (int gi = 0; gi < 2; ++gi) {
           const int gq = 2 * gi + half;  // 16-column group
-          if (gq * 16 < ntp) {
-            float hi[16], lo[16], d[16];
-            tmem_ld16(lane_base + 0 * ntp + gq * 16, hi);
-            tmem_ld16(lane_base + 1 * ntp + gq * 16, lo);
-            tmem_wait_ld();
+          if (gq * 16 < q.ntp) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) lo[j] *= 0.00390625f;
-#pragma unroll
-            for (int ord = 2; ord < kSlices; ++ord) {
-              tmem_ld16(lane_base + ord * ntp + gq * 16, d);
+            for (int sub = 0; sub < 2; ++sub) {
+              const int c0 = gq * 16 + 8 * sub;  // first of 8 columns
+              float t8[8], lo[8];
+              tmem_ld8(lane_base + 0 * q.ntp + c0, t8);
+              tmem_ld8(lane_base + 1 * q.ntp + c0, lo);
               tmem_wait_ld();
-              const float sc = pow2f(-8 * ord);
+              // order 0 (exact integers) into the double-float sums
 #pragma unroll
-              for (int j = 0; j < 16; ++j) lo[j] = fmaf(d[j], sc, lo[j]);
-            }
+              for (int j = 0; j < 8; ++j) {
+                const int qq = gi * 16 + 8 * sub + j;
+                const float x = t8[j] * pow2f(ea + ebw[c0 + j] - 14);
+                const float t = H[qq] + x;
+                const float bb = t - H[qq];
+                const float err = (H[qq] - (t - bb)) + (x - bb);
+                H[qq] = t;
+                L[qq] += err;
+              }
+              // orders 1..3, 256 times smaller each, as one FP32 correction
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float s = pow2f(ea + sm.eb[st][gq * 16 + j] - 14);
-              const float x = hi[j] * s;
-              const int q = gi * 16 + j;
-              const float t = H[q] + x;
-              const float bb = t - H[q];
-              const float err = (H[q] - (t - bb)) + (x - bb);
-              H[q] = t;
-              L[q] += fmaf(lo[j], s, err);
+              for (int ord = 2; ord < kSlices; ++ord) {
+                tmem_ld8(lane_base + ord * q.ntp + c0, t8);
+                tmem_wait_ld();
+                const float sc = pow2f(-8 * (ord - 1));
+#pragma unroll
+                for (int j = 0; j < 8; ++j) lo[j] = fmaf(t8[j], sc, lo[j]);
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const int qq = gi * 16 + 8 * sub + j;
+                L[qq] = fmaf(lo[j], pow2f(ea + ebw[c0 + j] - 22), L[qq]);
+              }
             }
           }
         }
         fence_before();
         __syncwarp();
-        if (lane == 0) ws::mbar_arrive(smem_u32(&sm.freed[st]));
+        if (lane == 0) ws::mbar_arrive(&sm.tmem_free[set]);
       }
-      if (!ok) break;
-      // (hi, lo) partial sums of this item's point range
-      const int grow = r0 + row_in_tile;
+      if (!run) break;
+      // (hi, lo) partial sums of this tile's window range
+      const int grow = it.tm * kM + row_in_tile;
       if (grow < b.m) {
-        float2* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n;
+        float2* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n + (int64_t)grow * b.n;
 #pragma unroll
         for (int gi = 0; gi < 2; ++gi) {
           const int gq = 2 * gi + half;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const int col = gq * 16 + j;
-            if (col < nt) {
-              out[(int64_t)grow * b.n + c0 + col] = make_float2(H[gi * 16 + j], L[gi * 16 + j]);
+            const int cc = gq * 16 + j;
+            if (cc < q.nt) {
+              const int col = q.formed ? q.pt->col[cc] : it.tn * kTileN + cc;
+              out[col] = make_float2(H[gi * 16 + j], L[gi * 16 + j]);
             }
           }
         }
@@ -730,7 +970,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1) contract_ws_kernel(const DevG
   }
   fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (warp == ws::kMmaWarp) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
   }
@@ -795,12 +1035,19 @@ cudaError_t prepare_kernels() {
   return cudaFuncSetAttribute(contract_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes());
 }
 
+cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
+                        const float* ops, uint8_t* packed, cudaStream_t s) {
+  if (n_jobs == 0) return cudaSuccess;
+  pack_kernel<<<(unsigned)n_jobs, 256, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                               int n_ctas, const short2* rows, const float* ops, float2* part, int* status,
-                               cudaStream_t s) {
+                               int n_ctas, const Panel* panels, const PairTile* ptiles, const float* ops,
+                               const uint8_t* packed, float2* part, int* status, cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  const size_t bytes = ws_smem_bytes();
-  contract_ws_kernel<<<n_ctas, ws::kThreads, bytes, s>>>(grids, blocks, items, n_items, rows, ops, part, status);
+  contract_ws_kernel<<<n_ctas, ws::kThreads, ws_smem_bytes(), s>>>(grids, blocks, items, n_items, panels, ptiles, ops,
+                                                                   packed, part, status);
   return cudaGetLastError();
 }
 

@@ -140,3 +140,18 @@ def test_launch_count_and_workspace(P, ctx):
     assert J.stats(oracle.S)["launches"] == 3 + 1
     assert J.workspace_bytes(oracle.S) < J.workspace_bytes(oracle.ALL)
     assert J.stats(oracle.S)["grids"] == 3 and J.stats(oracle.ALL)["grids"] == 6
+
+
+@pytest.mark.parametrize("make", [synth.h2_fp64, synth.triatomic_oh2, synth.c3h6])
+def test_issued_flops_bound_the_useful_work(P, ctx, make):
+    """The tensor-pipe roofline counts issued MMAs: ten slice products per useful product,
+    plus tile padding and the duplicated triangle of symmetric blocks, so never less than 20
+    FLOPs per useful contraction; on the large blocks of C3H6 padding stays under 2x.  The FP64
+    path issues at least the useful 2 FLOPs per contraction."""
+    job = make(0)
+    for prec, lo in ((P.MIXED, 20.0), (P.FP64, 2.0)):
+        J = P.Job.from_synth(ctx, job, prec)
+        st = J.stats(job.mask)
+        assert st["issued_flops"] >= lo * st["contractions"]
+        if make is synth.c3h6:
+            assert st["issued_flops"] <= 2 * lo * st["contractions"]
