@@ -57,6 +57,19 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def aggregate(times_s, units_per_rank, world, device="cuda"):
+    """Replicas (weak scaling): every rank processed `units_per_rank` in its own wall times
+    `times_s` (one per timed region); the job's time of a region is the slowest rank's, and its
+    throughput all ranks' units over that time.  Returns (max times, throughputs)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor(list(times_s), dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        times_s = [float(x) for x in t.tolist()]
+    return list(times_s), [world * u / t for u, t in zip(units_per_rank, times_s)]
+
+
 # ------------------------------------------------------------------------------ CPU oracle
 
 def oracle_sample(job):
@@ -301,12 +314,10 @@ def main():
     prof = J.profile_read()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    (t_max,), (value,) = aggregate([ms / 1e3], [st["contractions"] * args.steps], world)
+    ms = t_max * 1e3
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * st["contractions"] * args.steps / (ms / 1e3)
 
     # the same steps replayed from the job's captured CUDA graph
     graph = None
@@ -353,11 +364,7 @@ def main():
             J.compute_host(mask, ws, out, host, stream)
         e2e_s = time.perf_counter() - t0
     h2d, d2h = J.io_bytes(mask)
-    e2e_val = st["contractions"] * args.e2e_steps / e2e_s
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * st["contractions"] * args.e2e_steps / float(t.item())
+    _, (e2e_val,) = aggregate([e2e_s], [st["contractions"] * args.e2e_steps], world)
 
     # roofline of the dominant kernel, timed live inside the timed region
     kind = max(prof, key=lambda k: prof[k][0])

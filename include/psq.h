@@ -100,8 +100,8 @@ psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_
 
 /* Floating-point operations the contraction kernel issues in one psq_compute for mask (the
  * measure a tensor-pipe roofline counts; no paper counterpart).  PSQ_MIXED: every tensor-core
- * MMA of the 8-bit slice products, a 128-row tile padded to the 16-column multiple, 10 slice
- * products per 64-point chunk, each M x N x K MMA counting 2MNK.  PSQ_FP64: 2 x rows x cols x
+ * MMA of the 8-bit slice products, tiles of 128 rows x 64 columns whatever their fill, 10
+ * slice products per 64-point chunk, each M x N x K MMA counting 2MNK.  PSQ_FP64: 2 x rows x cols x
  * points summed over the computed blocks.  Errors: PSQ_ERR_ARG for NULL pointers or unknown
  * mask bits. */
 psq_status psq_job_issued_flops(const psq_job* job, unsigned mask, double* flops);

@@ -734,12 +734,14 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     int64_t mtiles = 0;
     for (auto& mb : P.mblocks)
       mtiles += (int64_t)((mb.m + 127) / 128) * (mb.b_panel >= 0 ? (mb.n + 63) / 64 : mb.n_btiles);
-    const int64_t want = 4LL * kSmCount;
+    // about 16 items per SM (a static round-robin then ends within ~6% of the mean), ranges
+    // of at least 4 windows
+    const int64_t want = 16LL * kSmCount;
     const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi) {
       MmaBlock& mb = P.mblocks[bi];
       const int64_t nwin = ((P.grids[mb.grid].K + 63) / 64 + 1) / 2;
-      const int64_t r0 = std::max<int64_t>(1, std::min<int64_t>(cr, (nwin + 7) / 8));
+      const int64_t r0 = std::max<int64_t>(1, std::min<int64_t>(cr, (nwin + 3) / 4));
       mb.win_per = (int)((nwin + r0 - 1) / r0);
       mb.n_ranges = (int)((nwin + mb.win_per - 1) / mb.win_per);
       mb.part_off = part;
@@ -757,13 +759,9 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     };
     std::stable_sort(P.mitems.begin(), P.mitems.end(),
                      [&](const GemmItem& x, const GemmItem& y) { return item_chunks(x) > item_chunks(y); });
-    // issued tensor work: per 64-point chunk of an item, 10 slice products of a 128 x ntp x 64 tile
-    for (const GemmItem& it : P.mitems) {
-      const MmaBlock& mb = P.mblocks[it.block];
-      const int nt = mb.b_panel >= 0 ? std::min(64, mb.n - it.tn * 64) : P.ptiles[mb.ptile_off + it.tn].ncols;
-      const int ntp = (nt + 15) & ~15;
-      P.issued_flops += (double)item_chunks(it) * 10.0 * 2.0 * 128.0 * ntp * 64.0;
-    }
+    // issued tensor work: per 64-point chunk of an item, the slice products of orders 0..3
+    // (10 of 128 x 64 x 64, issued as four MMAs of N = 256, 192, 128, 64)
+    for (const GemmItem& it : P.mitems) P.issued_flops += (double)item_chunks(it) * 10.0 * 2.0 * 128.0 * 64.0 * 64.0;
     P.elem_begin.resize(P.mblocks.size() + 1);
     P.elem_begin[0] = 0;
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi)

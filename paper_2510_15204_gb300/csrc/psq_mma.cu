@@ -8,15 +8,19 @@
 //    potentials (eq 16, incomplete gamma by its positive series below x = k) in FP32 as
 //    functions of x = zeta r (x from an FP32 hi+lo scale, first-order corrected); every
 //    constant factor of a row is left to FP64;
-//  * contract_ws_kernel: the weighted contraction of eq 9 on tcgen05 tensor cores.  Every
-//    operand row of a 64-point chunk is scaled by a power of two from its maximum and cut
-//    into four integer slices of at most 8 bits (exact in BF16).  Ten BF16 MMAs per K step
-//    accumulate the slice products by order (0..3) into four FP32 TMEM accumulators; all
-//    partial sums are integers below 2^24, so the FP32 accumulation is exact.  After each
-//    chunk the accumulators are scaled back and added into double-float (FP32 hi + lo)
-//    registers; each work item writes its point range's (hi, lo) sums, and reduce_mixed_kernel
-//    adds the ranges in FP64 and applies the FP64 constants of each row and column
-//    (normalisations, powers of zeta, a^3), which the FP32 values omit.
+//  * pack_kernel: every operand row that a contraction tile reads whole is scaled by a power
+//    of two per 128-point window (from the window's maximum) and cut into four integer
+//    slices of at most 8 bits (exact in BF16), stored as the tcgen05 shared-memory image;
+//  * contract_ws_kernel: the weighted contraction of eq 9 on tcgen05 tensor cores.  Packed
+//    tiles arrive by bulk copies; the 3-index operand chi_i chi_j is formed and sliced in
+//    shared memory from staged basis rows.  Per K step of 16 points four MMAs (A slice i
+//    against B slices 0..3-i, contiguous in shared memory) accumulate the slice products of
+//    orders 0..3 into four FP32 TMEM accumulators; all partial sums are integers below 2^23,
+//    so the FP32 accumulation is exact.  After each window the accumulators are scaled back
+//    and added into double-float (FP32 hi + lo) registers; each work item writes its point
+//    range's (hi, lo) sums, and reduce_mixed_kernel adds the ranges in FP64 and applies the
+//    FP64 constants of each row and column (normalisations, powers of zeta, a^3), which the
+//    FP32 values omit.
 #include "psq_internal.h"
 
 #include <cuda_bf16.h>
@@ -480,9 +484,10 @@ __device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)r * 128
 
 }  // namespace mma
 
-// One CTA per (panel, tile, 128-point window); thread (r, h) packs row r of the tile for
-// chunk 2w + h.  The two threads of a row share the window's scale.
-__global__ void __launch_bounds__(256) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
+// One CTA per (panel, tile, 128-point window), four threads per row: thread (r, qd) packs
+// points [32 qd, 32 qd + 32) of the window (chunk qd / 2, half qd % 2) of row r; the four
+// threads of a row share the window's scale.
+__global__ void __launch_bounds__(512, 2) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
                                                    int n_panels, const short2* __restrict__ rows,
                                                    const float* __restrict__ ops, uint8_t* __restrict__ packed) {
   using namespace mma;
@@ -495,25 +500,26 @@ __global__ void __launch_bounds__(256) pack_kernel(const DevGrid* __restrict__ g
   const Panel pn = panels[lo];
   const int64_t lj = job - pn.job_begin;
   const int t = (int)(lj / pn.nwin), w = (int)(lj % pn.nwin);
-  const int r = threadIdx.x >> 1, h = threadIdx.x & 1;
+  const int r = threadIdx.x >> 2, qd = threadIdx.x & 3;
   if (r >= pn.tr) return;  // whole warps
   const DevGrid& g = grids[pn.grid];
-  const int c = 2 * w + h;
+  const int c = 2 * w + (qd >> 1), hh = qd & 1;
   const int row = t * pn.tr + r;
+  const int64_t k0 = 64 * (int64_t)c + 32 * hh;  // first point of this thread
   const float* src = nullptr;
   const float* mul = nullptr;
   if (row < pn.nrows && c < pn.nch) {
     const short2 q = rows[pn.rows_off + row];
-    src = ops + g.op_off + (int64_t)q.x * g.ld + 64 * (int64_t)c;
-    if (q.y >= 0) mul = ops + g.op_off + (int64_t)q.y * g.ld + 64 * (int64_t)c;
+    src = ops + g.op_off + (int64_t)q.x * g.ld + k0;
+    if (q.y >= 0) mul = ops + g.op_off + (int64_t)q.y * g.ld + k0;
   }
-  const int64_t left = g.K - 64 * (int64_t)c;
-  float v[64];
-  if (src && left >= 64) {
+  const int64_t left = g.K - k0;
+  float v[32];
+  if (src && left >= 32) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     const float4* m4 = reinterpret_cast<const float4*>(mul);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 8; ++i) {
       float4 a = __ldg(s4 + i);
       if (mul) {
         const float4 b = __ldg(m4 + i);
@@ -523,15 +529,16 @@ __global__ void __launch_bounds__(256) pack_kernel(const DevGrid* __restrict__ g
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = (src && i < left) ? src[i] * (mul ? mul[i] : 1.0f) : 0.0f;
+    for (int i = 0; i < 32; ++i) v[i] = (src && i < left) ? src[i] * (mul ? mul[i] : 1.0f) : 0.0f;
   }
   float mx = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 64; ++i) mx = fmaxf(mx, fabsf(v[i]));
-  const unsigned pair_mask = 3u << ((threadIdx.x & 31) & ~1u);
-  mx = fmaxf(mx, __shfl_xor_sync(pair_mask, mx, 1));
+  for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[i]));
+  const unsigned quad_mask = 0xfu << ((threadIdx.x & 31) & ~3u);
+  mx = fmaxf(mx, __shfl_xor_sync(quad_mask, mx, 1));
+  mx = fmaxf(mx, __shfl_xor_sync(quad_mask, mx, 2));
   const int e = row_exponent(mx);
-  if (h == 0)
+  if (qd == 0)
     *reinterpret_cast<int*>(packed + pn.exp_off + (((int64_t)t * pn.nwin + w) * pn.tr + r) * 4) = e;
   const int rt = min(pn.tr, pn.nrows - t * pn.tr);  // rows stored for this tile
   if (c >= pn.nch || r >= rt) return;
@@ -539,11 +546,11 @@ __global__ void __launch_bounds__(256) pack_kernel(const DevGrid* __restrict__ g
   uint8_t* dst = packed + pn.pack_off + (int64_t)t * pn.nch * (4 * pn.tr * 128) + (int64_t)c * (4 * rt * 128);
   const int plane = rt * 128;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < 4; ++j) {
     uint4 wv[kSlices];
     slice8(v + 8 * j, sc, wv);
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(r, j)) = wv[k];
+    for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(r, 4 * hh + j)) = wv[k];
   }
 }
 
@@ -554,9 +561,10 @@ __global__ void __launch_bounds__(256) pack_kernel(const DevGrid* __restrict__ g
 //   warp 4       loader: bulk copies of the packed A tile (and packed B tile) of every 64-point
 //                chunk into a two-stage ring, and of the staged basis rows of formed B tiles
 //                (one copy per row and window);
-//   warps 0-3    producers: for a formed B, column c of the tile = product of two staged rows,
-//                sliced under one scale per column and window into the chunk's B stage (for a
-//                packed B they only pass each chunk on);
+//   warps 0-3    producers: for a formed B, column c of the tile = product of two staged rows;
+//                per window they find each column's scale, then slice chunk by chunk into the
+//                B stages, so that the MMAs of one chunk overlap the slicing of the next (for
+//                a packed B they only pass each chunk on);
 //   warp 5       MMA issue: per chunk 4 K-steps x 10 slice products (orders 0..3) into the
 //                window's TMEM accumulator set (4 orders x 64 columns; two sets);
 //   warps 8-15   fold: per window, the four order sums of their TMEM lane quadrant and column
@@ -577,7 +585,7 @@ struct Smem {
   alignas(1024) uint8_t b[2][mma::kSlices][mma::kTileN * 128];
   alignas(16) float raw[2][kPairTileRows][kRawStride];
   int eb[2][mma::kTileN];
-  int ebw[8][mma::kTileN];  // fold warp k: the column exponents of the current window
+  float sbw[8][mma::kTileN];  // fold warp k: the column scales of the current window
   alignas(8) uint64_t a_full[2], b_ready[2], stage_free[2], tmem_full[2], tmem_free[2], raw_full[2], raw_free[2];
   uint64_t drain;
   uint32_t tmem_base;
@@ -743,8 +751,11 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     }
   } else if (warp < 4) {
     // ------------------------------------------------------------------ producers
-    const int col = tid >> 1, h = tid & 1;
-    const unsigned pair_mask = 3u << ((tid & 31) & ~1u);
+    // eight consecutive lanes take eight columns of one half: the columns of a pair tile share
+    // their first row in groups of eight, so a quarter warp's loads are one broadcast and
+    // eight distinct rows (distinct bank groups); the two halves of a column are lanes l, l^8
+    const int col = (tid & 7) + 8 * (tid >> 4), h = (tid >> 3) & 1;
+    const unsigned pair_mask = (1u << (tid & 31)) | (1u << ((tid & 31) ^ 8));
     bool run = true;  // warp-uniform
     for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
       const GemmItem it = items[ii];
@@ -767,61 +778,68 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       for (int win = q.w0; win < q.w1 && run; ++win, ++w, ++rw) {
         const int nck = min(2, q.nch - 2 * win);
         const int rb = rw & 1, set = w & 1;
-        const uint32_t cc = c + h;  // this thread's chunk
         bool ok = ws::wait(&sm.raw_full[rb], (rw >> 1) & 1, &sm.abort);
         if (ok && w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort);
-        if (ok && h < nck && cc >= 2) ok = ws::wait(&sm.stage_free[cc & 1], ((cc - 2) >> 1) & 1, &sm.abort);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 5); break; }
-        const float* rx = sm.raw[rb][dx] + 64 * h;
-        const float* ry = sm.raw[rb][dy] + 64 * h;
-        // points of this thread's chunk that exist (none for a padding column)
-        const int64_t left = valid ? q.K - (128 * (int64_t)win + 64 * h) : 0;
-        float mx = 0.0f;
-        if (h < nck) {
+        // thread h owns points [32h, 32h + 32) of both chunks of the window: products once,
+        // the column's window maximum with its partner, then slices chunk by chunk
+        const int64_t wleft = valid ? q.K - 128 * (int64_t)win : 0;  // points of the window that exist
+        float v[2][32];
 #pragma unroll
-          for (int i = 0; i < 64; i += 4) {
-            const float4 a = *reinterpret_cast<const float4*>(rx + i);
-            const float4 bq = *reinterpret_cast<const float4*>(ry + i);
-            const float p0 = i + 0 < left ? a.x * bq.x : 0.0f, p1 = i + 1 < left ? a.y * bq.y : 0.0f;
-            const float p2 = i + 2 < left ? a.z * bq.z : 0.0f, p3 = i + 3 < left ? a.w * bq.w : 0.0f;
-            mx = fmaxf(fmaxf(mx, fabsf(p0)), fmaxf(fabsf(p1), fmaxf(fabsf(p2), fabsf(p3))));
+        for (int j = 0; j < 2; ++j) {
+          const int p0 = 64 * j + 32 * h;
+          const float* rx = sm.raw[rb][dx] + p0;
+          const float* ry = sm.raw[rb][dy] + p0;
+          const int64_t left = wleft - p0;
+          if (left >= 32) {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              const float4 a = *reinterpret_cast<const float4*>(rx + i);
+              const float4 bq = *reinterpret_cast<const float4*>(ry + i);
+              v[j][i] = a.x * bq.x; v[j][i + 1] = a.y * bq.y; v[j][i + 2] = a.z * bq.z; v[j][i + 3] = a.w * bq.w;
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[j][i] = i < left ? rx[i] * ry[i] : 0.0f;
           }
         }
-        mx = fmaxf(mx, __shfl_xor_sync(pair_mask, mx, 1));
+        float mx = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[j][i]));
+        mx = fmaxf(mx, __shfl_xor_sync(pair_mask, mx, 8));
         const int e = row_exponent(mx);
         if (h == 0) sm.eb[set][col] = e;
-        if (h < nck) {
-          const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
-          uint8_t* dst = sm.b[cc & 1][0];
+        const float sc_col = e == kZeroExp ? 0.0f : pow2f(7 - e);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            float v[8];
+        for (int j = 0; j < 2; ++j) {
+          if (j < nck && run) {
+            const bool okc = c < 2 || ws::wait(&sm.stage_free[c & 1], ((c - 2) >> 1) & 1, &sm.abort);
+            run = __all_sync(kFull, okc && !ws::aborted(sm));
+            if (!run) {
+              ws::fail(sm, status, 5);
+            } else {
+              uint8_t* dst = sm.b[c & 1][0];
 #pragma unroll
-            for (int u = 0; u < 8; u += 4) {
-              const float4 a = *reinterpret_cast<const float4*>(rx + 8 * j + u);
-              const float4 bq = *reinterpret_cast<const float4*>(ry + 8 * j + u);
-              const int i = 8 * j + u;
-              v[u + 0] = i + 0 < left ? a.x * bq.x : 0.0f;
-              v[u + 1] = i + 1 < left ? a.y * bq.y : 0.0f;
-              v[u + 2] = i + 2 < left ? a.z * bq.z : 0.0f;
-              v[u + 3] = i + 3 < left ? a.w * bq.w : 0.0f;
+              for (int g = 0; g < 4; ++g) {
+                uint4 wv[kSlices];
+                slice8(v[j] + 8 * g, sc_col, wv);
+#pragma unroll
+                for (int k = 0; k < kSlices; ++k)
+                  *reinterpret_cast<uint4*>(dst + k * (kTileN * 128) + swz(col, 4 * h + g)) = wv[k];
+              }
+              fence_async_smem();
+              __syncwarp();
+              if (lane == 0) ws::mbar_arrive(&sm.b_ready[c & 1]);
+              ++c;
             }
-            uint4 wv[kSlices];
-            slice8(v, sc, wv);
-#pragma unroll
-            for (int k = 0; k < kSlices; ++k)
-              *reinterpret_cast<uint4*>(dst + k * (kTileN * 128) + swz(col, j)) = wv[k];
           }
         }
-        fence_async_smem();
+        if (!run) break;
         __syncwarp();
-        if (lane == 0) {
-          ws::mbar_arrive(&sm.b_ready[c & 1]);
-          if (nck == 2) ws::mbar_arrive(&sm.b_ready[(c + 1) & 1]);
-          ws::mbar_arrive(&sm.raw_free[rb]);
-        }
-        c += nck;
+        if (lane == 0) ws::mbar_arrive(&sm.raw_free[rb]);
       }
     }
   } else if (warp == ws::kMmaWarp) {
@@ -830,7 +848,6 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       for (int ii = blockIdx.x; ii < n_items && !ws::aborted(sm); ii += gridDim.x) {
         const GemmItem it = items[ii];
         const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
-        const uint32_t idesc = make_idesc(q.ntp);
         bool ok = true;
         for (int win = q.w0; win < q.w1 && ok; ++win, ++w) {
           const int nck = min(2, q.nch - 2 * win);
@@ -843,17 +860,17 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             if (ok) ok = ws::wait(&sm.b_ready[s], (c >> 1) & 1, &sm.abort);
             if (!ok) break;
             fence_after();
+            // The B planes of a stage are contiguous (64 rows each), so plane i of A against
+            // planes 0..3-i of B is one MMA of N = 64 (4 - i) whose columns land on the order
+            // accumulators i..3 (order k at TMEM columns 64k..64k+63 of the set).
 #pragma unroll
             for (int k = 0; k < kChunk / 16; ++k) {
               const uint32_t ko = 32u * k;
+              const uint64_t db = make_desc(smem_u32(sm.b[s][0]) + ko);
 #pragma unroll
-              for (int ord = 0; ord < kSlices; ++ord) {
-#pragma unroll
-                for (int i = 0; i <= ord; ++i) {
-                  const uint64_t da = make_desc(smem_u32(sm.a[s][i]) + ko);
-                  const uint64_t db = make_desc(smem_u32(sm.b[s][ord - i]) + ko);
-                  mma_bf16(tset + ord * q.ntp, da, db, idesc, (j > 0 || k > 0 || i > 0) ? 1u : 0u);
-                }
+              for (int i = 0; i < kSlices; ++i) {
+                const uint64_t da = make_desc(smem_u32(sm.a[s][i]) + ko);
+                mma_bf16(tset + 64u * i, da, db, make_idesc(64 * (kSlices - i)), (j > 0 || k > 0 || i > 0) ? 1u : 0u);
               }
             }
             mma_commit(smem_u32(&sm.stage_free[s]));
@@ -886,23 +903,29 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       float H[32], L[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) { H[j] = 0.0f; L[j] = 0.0f; }
+      // the window's exponents (A rows from the packed panel, B columns from the packed panel,
+      // one per lane for this warp's 32 columns, or from the producers), loaded one window ahead
+      const int my_col = (2 * (lane >> 4) + half) * 16 + (lane & 15);
+      const int* ea_src = reinterpret_cast<const int*>(packed + pa.exp_off) + (int64_t)it.tm * pa.nwin * kM + row_in_tile;
+      const int* eb_src = pb ? reinterpret_cast<const int*>(packed + pb->exp_off) + (int64_t)it.tn * pb->nwin * kTileN + my_col
+                             : nullptr;
+      int ea_next = __ldg(ea_src + (int64_t)q.w0 * kM);
+      int eb_next = eb_src ? __ldg(eb_src + (int64_t)q.w0 * kTileN) : 0;
       for (int win = q.w0; win < q.w1; ++win, ++w) {
         const int set = w & 1;
-        // the window's exponents: A rows from the packed panel, B columns from the packed
-        // panel (one per lane, for this warp's 32 columns) or from the producers
-        const int ea = __ldg(reinterpret_cast<const int*>(packed + pa.exp_off) +
-                             ((int64_t)it.tm * pa.nwin + win) * kM + row_in_tile);
-        const int my_col = (2 * (lane >> 4) + half) * 16 + (lane & 15);
-        int eb_lane = 0;
-        if (pb)
-          eb_lane = __ldg(reinterpret_cast<const int*>(packed + pb->exp_off) +
-                          ((int64_t)it.tn * pb->nwin + win) * kTileN + my_col);
+        const int ea = ea_next, eb_lane = eb_next;
+        if (win + 1 < q.w1) {
+          ea_next = __ldg(ea_src + (int64_t)(win + 1) * kM);
+          if (eb_src) eb_next = __ldg(eb_src + (int64_t)(win + 1) * kTileN);
+        }
         const bool ok = ws::wait(&sm.tmem_full[set], (w >> 1) & 1, &sm.abort);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 7); break; }
         fence_after();
-        int* ebw = sm.ebw[ew];
-        ebw[my_col] = pb ? eb_lane : sm.eb[set][my_col];
+        // column scales 2^(e_b - 7) for this warp, row scale 2^(e_a - 7) for this thread
+        float* sbw = sm.sbw[ew];
+        sbw[my_col] = pow2f((pb ? eb_lane : sm.eb[set][my_col]) - 7);
+        const float sa = pow2f(ea - 7);
         __syncwarp();
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * 256u;
 #pragma unroll
@@ -912,34 +935,25 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
             for (int sub = 0; sub < 2; ++sub) {
               const int c0 = gq * 16 + 8 * sub;  // first of 8 columns
-              float t8[8], lo[8];
-              tmem_ld8(lane_base + 0 * q.ntp + c0, t8);
-              tmem_ld8(lane_base + 1 * q.ntp + c0, lo);
+              float o0[8], o1[8], o2[8], o3[8];
+              tmem_ld8(lane_base + 0 * kTileN + c0, o0);
+              tmem_ld8(lane_base + 1 * kTileN + c0, o1);
+              tmem_ld8(lane_base + 2 * kTileN + c0, o2);
+              tmem_ld8(lane_base + 3 * kTileN + c0, o3);
               tmem_wait_ld();
-              // order 0 (exact integers) into the double-float sums
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
                 const int qq = gi * 16 + 8 * sub + j;
-                const float x = t8[j] * pow2f(ea + ebw[c0 + j] - 14);
+                const float sc = sa * sbw[c0 + j];  // 2^(e_a + e_b - 14)
+                // order 0 (exact integers) into the double-float sum, orders 1..3 (each 256
+                // times smaller) as one FP32 correction
+                const float x = o0[j] * sc;
                 const float t = H[qq] + x;
                 const float bb = t - H[qq];
                 const float err = (H[qq] - (t - bb)) + (x - bb);
                 H[qq] = t;
-                L[qq] += err;
-              }
-              // orders 1..3, 256 times smaller each, as one FP32 correction
-#pragma unroll
-              for (int ord = 2; ord < kSlices; ++ord) {
-                tmem_ld8(lane_base + ord * q.ntp + c0, t8);
-                tmem_wait_ld();
-                const float sc = pow2f(-8 * (ord - 1));
-#pragma unroll
-                for (int j = 0; j < 8; ++j) lo[j] = fmaf(t8[j], sc, lo[j]);
-              }
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const int qq = gi * 16 + 8 * sub + j;
-                L[qq] = fmaf(lo[j], pow2f(ea + ebw[c0 + j] - 22), L[qq]);
+                const float lo = fmaf(o3[j], 5.9604644775390625e-8f, fmaf(o2[j], 1.52587890625e-5f, o1[j] * 0.00390625f));
+                L[qq] += fmaf(lo, sc, err);
               }
             }
           }
@@ -977,39 +991,36 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 }
 
 // FP64 reduction of the (hi, lo) range partials of the tensor-core blocks, times the FP64
-// constants of each element's row and column; one warp per element, fixed order.
+// constants of each element's row and column; one thread per element, ranges added in
+// order (consecutive threads read consecutive partials).
 __global__ void __launch_bounds__(256) reduce_mixed_kernel(const DevGrid* __restrict__ grids,
                                                            const MmaBlock* __restrict__ blocks, int n_blocks,
                                                            const int64_t* __restrict__ elem_begin, int64_t n_elems,
                                                            const short2* __restrict__ rows,
                                                            const double* __restrict__ rowc,
                                                            const float2* __restrict__ part, double* __restrict__ res) {
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (wid >= n_elems) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_elems) return;
   int lo = 0, hi = n_blocks;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (elem_begin[mid] <= wid) lo = mid; else hi = mid;
+    if (elem_begin[mid] <= idx) lo = mid; else hi = mid;
   }
   const MmaBlock b = blocks[lo];
-  const int64_t e = wid - elem_begin[lo];
+  const int64_t e = idx - elem_begin[lo];
   const int64_t mn = (int64_t)b.m * b.n;
+  const float2* p = part + b.part_off + e;
   double s = 0.0;
-  for (int c = lane; c < b.n_ranges; c += 32) {
-    const float2 v = part[b.part_off + c * mn + e];
+  for (int c = 0; c < b.n_ranges; ++c) {
+    const float2 v = __ldg(p + c * mn);
     s += (double)v.x + (double)v.y;
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) {
-    const int r = (int)(e / b.n), col = (int)(e % b.n);
-    const double* rc = rowc + grids[b.grid].rc_off;
-    const short2 qa = rows[b.a_off + r], qb = rows[b.b_off + col];
-    const double ca = rc[qa.x] * (qa.y >= 0 ? rc[qa.y] : 1.0);
-    const double cb = rc[qb.x] * (qb.y >= 0 ? rc[qb.y] : 1.0);
-    res[b.res_off + e] = s * ca * cb;
-  }
+  const int r = (int)(e / b.n), col = (int)(e % b.n);
+  const double* rc = rowc + grids[b.grid].rc_off;
+  const short2 qa = rows[b.a_off + r], qb = rows[b.b_off + col];
+  const double ca = rc[qa.x] * (qa.y >= 0 ? rc[qa.y] : 1.0);
+  const double cb = rc[qb.x] * (qb.y >= 0 ? rc[qb.y] : 1.0);
+  res[b.res_off + e] = s * ca * cb;
 }
 
 // ------------------------------------------------------------------ launchers
@@ -1038,7 +1049,7 @@ cudaError_t prepare_kernels() {
 cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
                         const float* ops, uint8_t* packed, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
-  pack_kernel<<<(unsigned)n_jobs, 256, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
+  pack_kernel<<<(unsigned)n_jobs, 512, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
   return cudaGetLastError();
 }
 
@@ -1055,8 +1066,7 @@ cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, in
                                 int64_t n_elems, const short2* rows, const double* rowc, const float2* part,
                                 double* res, cudaStream_t s) {
   if (n_elems == 0) return cudaSuccess;
-  const int64_t threads = n_elems * 32;
-  reduce_mixed_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(grids, blocks, n_blocks, elem_begin, n_elems,
+  reduce_mixed_kernel<<<(unsigned)((n_elems + 255) / 256), 256, 0, s>>>(grids, blocks, n_blocks, elem_begin, n_elems,
                                                                          rows, rowc, part, res);
   return cudaGetLastError();
 }
