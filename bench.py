@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default work split")
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the step benchmark")
     ap.add_argument("--rates", default="20,100", help="serving: Poisson arrival rates (jobs/s)")
     ap.add_argument("--jobs", type=int, default=24, help="serving: jobs per rate")
@@ -291,13 +292,18 @@ def main():
     ctx = P.Context(local)
     prec = P.MIXED if args.precision == "mixed" else P.FP64
     J = P.Job.from_synth(ctx, job, prec)
-    st = J.stats(mask)
-    ws, out = J.alloc(mask)
+    ws, out = J.alloc(mask, headroom=0.25)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        # the work split is tuned on this job during warm-up (candidates that fit the workspace)
+        tuned = None
+        if not args.no_autotune:
+            split, tms = J.autotune(mask, ws, out, stream)
+            tuned = {"work_split": split, "ms": tms}
         for _ in range(max(args.warmup, 3)):
             J.compute(mask, ws, out, stream)
     torch.cuda.synchronize()
+    st = J.stats(mask)
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local)
@@ -404,6 +410,7 @@ def main():
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "graph": graph,
+        "autotune": tuned,
         "plain_fp64": plain,
         "gpu_launches": st["launches"] * args.steps,
         "clocks": clk,

@@ -98,6 +98,18 @@ psq_status psq_job_workspace(const psq_job* job, unsigned mask, size_t* bytes);
 psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_t* n_points,
                          double* contractions, int* launches);
 
+/* Autotuning (the batched launch's work split; no paper counterpart).  Plans mask with each
+ * candidate work split (PSQ_MIXED: 4, 8, 16 or 32 contraction work items per SM; PSQ_FP64: 2,
+ * 4, 8 or 16 waves of CTAs per SM), runs each candidate that fits ws_bytes once to warm up
+ * and three times under CUDA events on stream, keeps the fastest as the job's plan for mask
+ * (later psq_compute / psq_compute_graph / psq_job_workspace calls use it; graphs captured
+ * before are dropped) and returns its split and mean milliseconds (either pointer may be
+ * NULL).  Synchronises the stream.  d_out holds valid results afterwards (of the last
+ * candidate run).  Errors: PSQ_ERR_ARG for a planning-only context, NULL or misaligned
+ * arguments; PSQ_ERR_OOM when no candidate fits ws_bytes; PSQ_ERR_CUDA on a failed launch. */
+psq_status psq_job_autotune(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
+                            void* stream, int* work_split, float* best_ms);
+
 /* Floating-point operations the contraction kernel issues in one psq_compute for mask (the
  * measure a tensor-pipe roofline counts; no paper counterpart).  PSQ_MIXED: every tensor-core
  * MMA of the 8-bit slice products, tiles of 128 rows x 64 columns whatever their fill, 10

@@ -56,6 +56,8 @@ SIGNATURES = [
     ("psq_job_stats", _I, [_VP, _U, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     ("psq_job_issued_flops", _I, [_VP, _U, ctypes.POINTER(ctypes.c_double)]),
+    ("psq_job_autotune", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP, ctypes.POINTER(_I),
+                              ctypes.POINTER(ctypes.c_float)]),
     ("psq_compute", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP]),
     ("psq_compute_host", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     ("psq_compute_graph", _I, [_VP, _U, _VP, _SZ, ctypes.POINTER(_VP), _VP]),
@@ -188,11 +190,13 @@ class Job:
         shapes = {"S": (nb, nb), "T": (nb, nb), "V": (nb, nb), "J2": (na, na), "J3": (na, nb, nb)}
         return {k: shapes[k] for i, k in enumerate(CLASSES) if (mask >> i) & 1}
 
-    def alloc(self, mask=ALL, device=None):
-        """Device workspace and output tensors for mask (torch allocations)."""
+    def alloc(self, mask=ALL, device=None, headroom=0.0):
+        """Device workspace and output tensors for mask (torch allocations); headroom is the
+        extra fraction of workspace, room for the candidates of autotune()."""
         import torch
         dev = torch.device("cuda", self.ctx.device if device is None else device)
-        ws = torch.empty(max(256, self.workspace_bytes(mask)), dtype=torch.uint8, device=dev)
+        need = self.workspace_bytes(mask)
+        ws = torch.empty(max(256, int(need * (1.0 + headroom))), dtype=torch.uint8, device=dev)
         out = {k: torch.empty(s, dtype=torch.float64, device=dev) for k, s in self.out_shapes(mask).items()}
         return ws, out
 
@@ -209,6 +213,17 @@ class Job:
         _check(lib().psq_compute(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), ws.numel(), ptrs,
                                  _stream_ptr(stream)))
         return out
+
+    def autotune(self, mask, ws, out, stream=None):
+        """Times the candidate work splits on ws/out and keeps the fastest plan for mask;
+        returns (chosen split, mean ms of one compute).  Synchronises the stream."""
+        ptrs = (ctypes.c_void_p * 5)()
+        for i, k in enumerate(CLASSES):
+            ptrs[i] = out[k].data_ptr() if k in out else None
+        split, ms = ctypes.c_int(), ctypes.c_float()
+        _check(lib().psq_job_autotune(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), ws.numel(), ptrs,
+                                      _stream_ptr(stream), ctypes.byref(split), ctypes.byref(ms)))
+        return split.value, ms.value
 
     def compute_graph(self, mask, ws, out, stream):
         """compute() through the job's captured CUDA graph (stream must not be the default)."""

@@ -150,6 +150,7 @@ struct Plan {
   double contractions = 0;
   double issued_flops = 0;
   int launches = 0;
+  int work_split = 16;  // work items (mixed) or 8-CTA waves (FP64) per SM; psq_job_autotune picks it
   ~Plan() {
     if (staging && pinned) cudaFreeHost(staging);
     if (staging && !pinned) std::free(staging);
@@ -169,6 +170,7 @@ struct psq_job {
   std::vector<DevShell> dbs, das;
   int nbf = 0, naux = 0;
   std::map<unsigned, std::unique_ptr<Plan>> plans;
+  std::map<unsigned, int> work_split;  // per mask, chosen by psq_job_autotune
   std::mutex mu;
   // launch timing: events recorded on the compute stream, read back on request
   struct ProfRec { int kind; cudaEvent_t ev; };
@@ -471,7 +473,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     // chunking: enough CTAs for several waves, chunks of at least 2048 points
     int64_t tiles = 0;
     for (auto& b : P.gblocks) tiles += (int64_t)((b.m + kTile - 1) / kTile) * ((b.n + kTile - 1) / kTile);
-    const int64_t want = 2LL * kSmCount * 8;
+    const int64_t want = 2LL * kSmCount * P.work_split;
     const int cglob = (int)std::max<int64_t>(1, tiles > 0 ? (want + tiles - 1) / tiles : 1);
     for (size_t bi = 0; bi < P.gblocks.size(); ++bi) {
       GemmBlock& b = P.gblocks[bi];
@@ -734,9 +736,9 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     int64_t mtiles = 0;
     for (auto& mb : P.mblocks)
       mtiles += (int64_t)((mb.m + 127) / 128) * (mb.b_panel >= 0 ? (mb.n + 63) / 64 : mb.n_btiles);
-    // about 16 items per SM (a static round-robin then ends within ~6% of the mean), ranges
-    // of at least 4 windows
-    const int64_t want = 16LL * kSmCount;
+    // work_split items per SM (16 by default: a static round-robin then ends within ~6% of
+    // the mean), ranges of at least 4 windows
+    const int64_t want = (int64_t)P.work_split * kSmCount;
     const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi) {
       MmaBlock& mb = P.mblocks[bi];
@@ -967,6 +969,9 @@ psq_status get_plan(psq_job* j, unsigned mask, Plan** out) {
   }
   std::unique_ptr<Plan> p(new (std::nothrow) Plan());
   if (!p) return fail(PSQ_ERR_OOM, "plan allocation failed");
+  auto ws = j->work_split.find(mask);
+  if (ws != j->work_split.end()) p->work_split = ws->second;
+  else p->work_split = j->prec == PSQ_MIXED ? 16 : 8;
   psq_status st = make_plan(j, mask, *p);
   if (st != PSQ_OK) return st;
   *out = p.get();
@@ -1228,6 +1233,10 @@ size_t psq::status_offset(psq_job* job, unsigned mask) {
   return it == job->plans.end() ? 0 : it->second->o_status;
 }
 
+namespace {
+psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_out[5], cudaStream_t s);
+}
+
 psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
                            void* stream, bool plan_must_exist) {
   if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
@@ -1251,8 +1260,13 @@ psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_
   if (!d_workspace || ws_bytes < P->ws_bytes)
     return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->ws_bytes);
   if ((uintptr_t)d_workspace % 256) return fail(PSQ_ERR_ARG, "workspace must be 256-byte aligned");
-  cudaStream_t s = (cudaStream_t)stream;
-  char* ws = (char*)d_workspace;
+  return run_plan(job, P, mask, (char*)d_workspace, d_out, (cudaStream_t)stream);
+}
+
+namespace {
+
+// The launch sequence of one psq_compute on plan P (arguments checked by the caller).
+psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_out[5], cudaStream_t s) {
   CUDA_TRY(mark(job, 0, s));
   CUDA_TRY(cudaMemcpyAsync(ws, P->staging, P->table_bytes, cudaMemcpyHostToDevice, s));
   const LaunchTables t = tables_at(*P, ws);
@@ -1308,7 +1322,88 @@ psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_
   return PSQ_OK;
 }
 
+}  // namespace
+
 extern "C" {
+
+psq_status psq_job_autotune(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
+                            void* stream, int* work_split, float* best_ms) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  if (job->ctx->device < 0) return fail(PSQ_ERR_ARG, "the job's context has no device (planning only)");
+  if (mask & ~31u) return fail(PSQ_ERR_ARG, "mask 0x%x has unknown bits", mask);
+  if (mask == 0) return fail(PSQ_ERR_ARG, "mask is empty");
+  if (!d_out) return fail(PSQ_ERR_ARG, "d_out is NULL");
+  for (int c = 0; c < 5; ++c)
+    if ((mask >> c) & 1 && !d_out[c]) return fail(PSQ_ERR_ARG, "output %d is NULL", c);
+  if (!d_workspace || (uintptr_t)d_workspace % 256) return fail(PSQ_ERR_ARG, "workspace NULL or not 256-byte aligned");
+  // candidates: work items per SM (mixed) or 8-CTA waves per SM (FP64)
+  static const int kMixed[] = {4, 8, 16, 32};
+  static const int kFp64[] = {2, 4, 8, 16};
+  const bool mixed = job->prec == PSQ_MIXED;
+  const int* cand = mixed ? kMixed : kFp64;
+  const int n_cand = 4;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(PSQ_ERR_CUDA, "cudaEventCreate failed");
+  }
+  const bool prof = job->prof_on;
+  job->prof_on = false;  // the trial runs stay out of the launch timing record
+  std::unique_ptr<Plan> best;
+  float best_t = 0.0f;
+  psq_status st = PSQ_OK;
+  for (int k = 0; k < n_cand && st == PSQ_OK; ++k) {
+    std::unique_ptr<Plan> p(new (std::nothrow) Plan());
+    if (!p) { st = fail(PSQ_ERR_OOM, "plan allocation failed"); break; }
+    p->work_split = cand[k];
+    st = make_plan(job, mask, *p);
+    if (st != PSQ_OK) break;
+    if (p->ws_bytes > ws_bytes) continue;  // does not fit the caller's workspace
+    char* ws = (char*)d_workspace;
+    st = run_plan(job, p.get(), mask, ws, d_out, s);  // warm-up
+    for (int r = 0; r < 3 && st == PSQ_OK; ++r) {
+      if (r == 0 && cudaEventRecord(e0, s) != cudaSuccess) st = fail(PSQ_ERR_CUDA, "cudaEventRecord failed");
+      if (st == PSQ_OK) st = run_plan(job, p.get(), mask, ws, d_out, s);
+    }
+    if (st != PSQ_OK) break;
+    float ms = 0.0f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = fail(PSQ_ERR_CUDA, "timing a candidate failed");
+      break;
+    }
+    ms /= 3.0f;
+    if (!best || ms < best_t) {
+      best_t = ms;
+      best = std::move(p);
+    }
+  }
+  job->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PSQ_OK) return st;
+  if (!best) return fail(PSQ_ERR_OOM, "no candidate plan fits a workspace of %zu bytes", ws_bytes);
+  const int chosen = best->work_split;
+  {
+    std::lock_guard<std::mutex> lk(job->mu);
+    job->plans[mask] = std::move(best);
+    job->work_split[mask] = chosen;
+    // graphs captured with the previous plan of this mask are stale
+    for (auto it = job->graphs.begin(); it != job->graphs.end();) {
+      if (it->first.mask == mask) {
+        cudaGraphExecDestroy(it->second);
+        it = job->graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  if (work_split) *work_split = chosen;
+  if (best_ms) *best_ms = best_t;
+  return PSQ_OK;
+}
 
 psq_status psq_compute_graph(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
                              void* stream) {

@@ -472,11 +472,11 @@ __device__ __forceinline__ void slice8(const float* v, float sc, uint4* w) {
   for (int k = 0; k < kSlices; ++k) w[k] = make_uint4(o[k][0], o[k][1], o[k][2], o[k][3]);
 }
 
-// Exponent e with max < 2^e (frexp), or kZeroExp for a row that is zero (or below 2^-110).
+// Exponent e with mx < 2^e <= 2 mx (frexp's), read from the exponent bits, or kZeroExp for
+// a row that is zero (or below 2^-110; subnormal maxima count as zero).
 __device__ __forceinline__ int row_exponent(float mx) {
-  int e = 0;
-  if (mx > 0.0f) frexpf(mx, &e);
-  return (!(mx > 0.0f) || e < -110) ? kZeroExp : e;
+  const int e = (int)(__float_as_uint(mx) >> 23) - 126;  // mx >= 0
+  return e < -110 ? kZeroExp : e;
 }
 
 // Byte offset of 16-byte group j of row r in a 128-byte-row swizzled operand tile.
@@ -561,10 +561,10 @@ __global__ void __launch_bounds__(512, 2) pack_kernel(const DevGrid* __restrict_
 //   warp 4       loader: bulk copies of the packed A tile (and packed B tile) of every 64-point
 //                chunk into a two-stage ring, and of the staged basis rows of formed B tiles
 //                (one copy per row and window);
-//   warps 0-3    producers: for a formed B, column c of the tile = product of two staged rows;
-//                per window they find each column's scale, then slice chunk by chunk into the
-//                B stages, so that the MMAs of one chunk overlap the slicing of the next (for
-//                a packed B they only pass each chunk on);
+//   warps 0-3, 6, 7  producers: for a formed B, column c of the tile = product of two staged
+//                rows; per window they find each column's scale, then slice chunk by chunk
+//                into the B stages, so that the MMAs of one chunk overlap the slicing of the
+//                next (for a packed B they only pass each chunk on);
 //   warp 5       MMA issue: per chunk 4 K-steps x 10 slice products (orders 0..3) into the
 //                window's TMEM accumulator set (4 orders x 64 columns; two sets);
 //   warps 8-15   fold: per window, the four order sums of their TMEM lane quadrant and column
@@ -674,12 +674,12 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
       ws::mbar_init(&sm.a_full[s], 1);
-      ws::mbar_init(&sm.b_ready[s], 4);
+      ws::mbar_init(&sm.b_ready[s], 6);
       ws::mbar_init(&sm.stage_free[s], 1);
       ws::mbar_init(&sm.tmem_full[s], 1);
       ws::mbar_init(&sm.tmem_free[s], 8);
       ws::mbar_init(&sm.raw_full[s], 1);
-      ws::mbar_init(&sm.raw_free[s], 4);
+      ws::mbar_init(&sm.raw_free[s], 6);
     }
     ws::mbar_init(&sm.drain, 1);
     sm.abort = 0;
@@ -749,13 +749,16 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       for (int k = last_a; k >= 0 && k > last_a - 2; --k) ws::wait(&sm.a_full[k & 1], (k >> 1) & 1);
       for (int k = last_raw; k >= 0 && k > last_raw - 2; --k) ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1);
     }
-  } else if (warp < 4) {
+  } else if (warp < 4 || warp == 6 || warp == 7) {
     // ------------------------------------------------------------------ producers
-    // eight consecutive lanes take eight columns of one half: the columns of a pair tile share
-    // their first row in groups of eight, so a quarter warp's loads are one broadcast and
-    // eight distinct rows (distinct bank groups); the two halves of a column are lanes l, l^8
-    const int col = (tid & 7) + 8 * (tid >> 4), h = (tid >> 3) & 1;
-    const unsigned pair_mask = (1u << (tid & 31)) | (1u << ((tid & 31) ^ 8));
+    // Six warps.  A window's 64 columns are 16 rounds of 4 columns; producer warp pw takes
+    // rounds pw, pw + 6, pw + 12.  In a round, eight lanes share a column, lane g owning
+    // points 8g..8g+7 of both chunks: they read contiguous 32-byte pieces of the column's two
+    // rows (one row per quarter warp), find the column's window maximum by shuffles, and
+    // write the eight 16-byte groups of the column's 128-byte row in each plane.
+    const int pw = warp < 4 ? warp : warp - 2;
+    const int g = lane & 7;
+    const unsigned col_mask = 0xffu << (lane & 24);
     bool run = true;  // warp-uniform
     for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
       const GemmItem it = items[ii];
@@ -773,8 +776,17 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         }
         continue;
       }
-      const bool valid = col < q.nt;
-      const int dx = valid ? q.pt->dx[col] : 0, dy = valid ? q.pt->dy[col] : 0;
+      // this lane's columns (one per round) and their two rows
+      int colr[3], dxr[3], dyr[3];
+      bool validr[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int R = pw + 6 * r;
+        colr[r] = 4 * R + (lane >> 3);
+        validr[r] = R < 16 && colr[r] < q.nt;
+        dxr[r] = validr[r] ? q.pt->dx[colr[r]] : 0;
+        dyr[r] = validr[r] ? q.pt->dy[colr[r]] : 0;
+      }
       for (int win = q.w0; win < q.w1 && run; ++win, ++w, ++rw) {
         const int nck = min(2, q.nch - 2 * win);
         const int rb = rw & 1, set = w & 1;
@@ -782,37 +794,45 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         if (ok && w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 5); break; }
-        // thread h owns points [32h, 32h + 32) of both chunks of the window: products once,
-        // the column's window maximum with its partner, then slices chunk by chunk
-        const int64_t wleft = valid ? q.K - 128 * (int64_t)win : 0;  // points of the window that exist
-        float v[2][32];
+        const int64_t wleft = q.K - 128 * (int64_t)win;  // points of the window that exist
+        float v[3][2][8];
+        float sc[3], mxr[3];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int p0 = 64 * j + 32 * h;
-          const float* rx = sm.raw[rb][dx] + p0;
-          const float* ry = sm.raw[rb][dy] + p0;
-          const int64_t left = wleft - p0;
-          if (left >= 32) {
+        for (int r = 0; r < 3; ++r) {
+          float mx = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              const float4 a = *reinterpret_cast<const float4*>(rx + i);
-              const float4 bq = *reinterpret_cast<const float4*>(ry + i);
-              v[j][i] = a.x * bq.x; v[j][i + 1] = a.y * bq.y; v[j][i + 2] = a.z * bq.z; v[j][i + 3] = a.w * bq.w;
+          for (int j = 0; j < 2; ++j) {
+            const int p0 = 64 * j + 8 * g;
+            const float* rx = sm.raw[rb][dxr[r]] + p0;
+            const float* ry = sm.raw[rb][dyr[r]] + p0;
+            const int64_t left = validr[r] ? wleft - p0 : 0;
+            if (left >= 8) {
+              const float4 a0 = *reinterpret_cast<const float4*>(rx);
+              const float4 a1 = *reinterpret_cast<const float4*>(rx + 4);
+              const float4 b0 = *reinterpret_cast<const float4*>(ry);
+              const float4 b1 = *reinterpret_cast<const float4*>(ry + 4);
+              v[r][j][0] = a0.x * b0.x; v[r][j][1] = a0.y * b0.y; v[r][j][2] = a0.z * b0.z; v[r][j][3] = a0.w * b0.w;
+              v[r][j][4] = a1.x * b1.x; v[r][j][5] = a1.y * b1.y; v[r][j][6] = a1.z * b1.z; v[r][j][7] = a1.w * b1.w;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) v[r][j][i] = i < left ? rx[i] * ry[i] : 0.0f;
             }
-          } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[j][i] = i < left ? rx[i] * ry[i] : 0.0f;
+            for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(v[r][j][i]));
           }
+          mxr[r] = mx;
         }
-        float mx = 0.0f;
+        // the column maxima over the eight lanes of each column, the three rounds interleaved
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int d = 1; d < 8; d <<= 1)
 #pragma unroll
-          for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[j][i]));
-        mx = fmaxf(mx, __shfl_xor_sync(pair_mask, mx, 8));
-        const int e = row_exponent(mx);
-        if (h == 0) sm.eb[set][col] = e;
-        const float sc_col = e == kZeroExp ? 0.0f : pow2f(7 - e);
+          for (int r = 0; r < 3; ++r) mxr[r] = fmaxf(mxr[r], __shfl_xor_sync(col_mask, mxr[r], d));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int e = row_exponent(mxr[r]);
+          if (g == 0 && pw + 6 * r < 16) sm.eb[set][colr[r]] = e;
+          sc[r] = e == kZeroExp ? 0.0f : pow2f(7 - e);
+        }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           if (j < nck && run) {
@@ -823,12 +843,14 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             } else {
               uint8_t* dst = sm.b[c & 1][0];
 #pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                uint4 wv[kSlices];
-                slice8(v[j] + 8 * g, sc_col, wv);
+              for (int r = 0; r < 3; ++r) {
+                if (pw + 6 * r < 16) {
+                  uint4 wv[kSlices];
+                  slice8(v[r][j], sc[r], wv);
 #pragma unroll
-                for (int k = 0; k < kSlices; ++k)
-                  *reinterpret_cast<uint4*>(dst + k * (kTileN * 128) + swz(col, 4 * h + g)) = wv[k];
+                  for (int k = 0; k < kSlices; ++k)
+                    *reinterpret_cast<uint4*>(dst + k * (kTileN * 128) + swz(colr[r], g)) = wv[k];
+                }
               }
               fence_async_smem();
               __syncwarp();

@@ -155,3 +155,11 @@ def test_issued_flops_bound_the_useful_work(P, ctx, make):
         assert st["issued_flops"] >= lo * st["contractions"]
         if make is synth.c3h6:
             assert st["issued_flops"] <= 2 * lo * st["contractions"]
+
+
+def test_autotune_needs_a_device(P, ctx):
+    import ctypes
+    J = P.Job.from_synth(ctx, synth.h2_fp64(0))
+    ptrs = (ctypes.c_void_p * 5)()
+    st = P.lib().psq_job_autotune(J.handle, oracle.ALL, None, 0, ptrs, None, None, None)
+    assert st == 1  # PSQ_ERR_ARG: planning-only context
