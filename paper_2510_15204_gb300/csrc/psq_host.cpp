@@ -546,7 +546,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       pn.exp_off = P.pack_bytes;
       P.pack_bytes += (int64_t)align_up((size_t)pn.n_tiles * pn.nwin * tr * 4, 256);
       pn.job_begin = P.n_pack_jobs;
-      P.n_pack_jobs += (int64_t)pn.n_tiles * pn.nwin;
+      P.n_pack_jobs += (int64_t)pn.n_tiles * pn.nwin * (tr / 64);  // 64-row groups
       P.panels.push_back(pn);
       return (int)P.panels.size() - 1;
     };

@@ -86,7 +86,7 @@ struct Panel {
   int tr, n_tiles;
   int nch, nwin;
   int64_t pack_off, exp_off;
-  int64_t job_begin;  // first (tile, window) packing job of this panel in a prefix over panels
+  int64_t job_begin;  // first packing job (tile, window, 64-row group) of this panel, prefix over panels
 };
 constexpr int kZeroExp = -100000;
 

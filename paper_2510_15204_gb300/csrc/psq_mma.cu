@@ -484,10 +484,10 @@ __device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)r * 128
 
 }  // namespace mma
 
-// One CTA per (panel, tile, 128-point window), four threads per row: thread (r, qd) packs
-// points [32 qd, 32 qd + 32) of the window (chunk qd / 2, half qd % 2) of row r; the four
-// threads of a row share the window's scale.
-__global__ void __launch_bounds__(512, 2) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
+// One CTA per (panel, tile, 128-point window, 64-row group), four threads per row: thread
+// (r, qd) packs points [32 qd, 32 qd + 32) of the window (chunk qd / 2, half qd % 2) of row r;
+// the four threads of a row share the window's scale.
+__global__ void __launch_bounds__(256, 4) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
                                                    int n_panels, const short2* __restrict__ rows,
                                                    const float* __restrict__ ops, uint8_t* __restrict__ packed) {
   using namespace mma;
@@ -498,10 +498,11 @@ __global__ void __launch_bounds__(512, 2) pack_kernel(const DevGrid* __restrict_
     if (panels[mid].job_begin <= job) lo = mid; else hi = mid;
   }
   const Panel pn = panels[lo];
+  const int groups = pn.tr / 64;
   const int64_t lj = job - pn.job_begin;
-  const int t = (int)(lj / pn.nwin), w = (int)(lj % pn.nwin);
-  const int r = threadIdx.x >> 2, qd = threadIdx.x & 3;
-  if (r >= pn.tr) return;  // whole warps
+  const int t = (int)(lj / ((int64_t)pn.nwin * groups));
+  const int w = (int)((lj / groups) % pn.nwin), grp = (int)(lj % groups);
+  const int r = 64 * grp + (threadIdx.x >> 2), qd = threadIdx.x & 3;
   const DevGrid& g = grids[pn.grid];
   const int c = 2 * w + (qd >> 1), hh = qd & 1;
   const int row = t * pn.tr + r;
@@ -1071,7 +1072,7 @@ cudaError_t prepare_kernels() {
 cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
                         const float* ops, uint8_t* packed, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
-  pack_kernel<<<(unsigned)n_jobs, 512, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
+  pack_kernel<<<(unsigned)n_jobs, 256, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
   return cudaGetLastError();
 }
 
