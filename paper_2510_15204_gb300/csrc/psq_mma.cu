@@ -154,9 +154,7 @@ __device__ __forceinline__ float ipowf(float x, int n) {
 //   chi: x^(n-1) e^-x;  lap chi: [(n(n-1) - l(l+1))/x^2 - 2n/x + 1] x^(n-1) e^-x;
 //   V^P: gamma(n+l+2, x)/x^(l+1) + Gamma(n-l+1, x) x^l.
 // x = xh + xl (FP32 pair); the result is corrected to first order in xl.
-__device__ __forceinline__ float radial_x(int kind, int n, int l, float xh, float xl) {
-  const float ex = expf(-xh);
-  const float ix = 1.0f / xh;
+__device__ __forceinline__ float radial_x_e(int kind, int n, int l, float xh, float xl, float ex, float ix) {
   if (kind == 2) {
     const int k1 = n + l + 2, k2 = n - l + 1;
     float inner;
@@ -189,6 +187,10 @@ __device__ __forceinline__ float radial_x(int kind, int n, int l, float xh, floa
   return fmaf(xl, df, f) * gc;
 }
 
+__device__ __forceinline__ float radial_x(int kind, int n, int l, float xh, float xl) {
+  return radial_x_e(kind, n, l, xh, xl, expf(-xh), 1.0f / xh);
+}
+
 // Rows of the shells [s0, s1) of one centre: kind 0 chi, 1 lap chi, 2 V^P.  xi[k] is the
 // (hi, lo) FP32 pair of the scale that turns rho into x for shell s0 + k.
 __device__ __forceinline__ void eval_shells_x(const DevShell* __restrict__ sh, const float2* __restrict__ xi,
@@ -202,6 +204,28 @@ __device__ __forceinline__ void eval_shells_x(const DevShell* __restrict__ sh, c
     const float radial = radial_x(kind, q.n, q.l, xh, xl);
     const int base = q.l * q.l + q.l;
     for (int m = -q.l; m <= q.l; ++m) out[(int64_t)(row0 + q.fn0 + q.l + m) * ld + p] = radial * Y[base + m];
+  }
+}
+
+// The same for two row kinds of the same shells (chi and lap chi, or chi and V^P) at once:
+// x, e^-x and 1/x are shared.
+__device__ __forceinline__ void eval_shells_x2(const DevShell* __restrict__ sh, const float2* __restrict__ xi,
+                                               int s0, int s1, float rho, const float* Y, float* __restrict__ out,
+                                               int64_t ld, int64_t p, int row_a, int kind_a, int row_b,
+                                               int kind_b) {
+  for (int s = s0; s < s1; ++s) {
+    const DevShell q = sh[s];
+    const float2 z = xi[s - s0];
+    const float xh = z.x * rho;
+    const float xl = fmaf(z.x, rho, -xh) + z.y * rho;
+    const float ex = expf(-xh), ix = 1.0f / xh;
+    const float ra = radial_x_e(kind_a, q.n, q.l, xh, xl, ex, ix);
+    const float rb = radial_x_e(kind_b, q.n, q.l, xh, xl, ex, ix);
+    const int base = q.l * q.l + q.l;
+    for (int m = -q.l; m <= q.l; ++m) {
+      out[(int64_t)(row_a + q.fn0 + q.l + m) * ld + p] = ra * Y[base + m];
+      out[(int64_t)(row_b + q.fn0 + q.l + m) * ld + p] = rb * Y[base + m];
+    }
   }
 }
 
@@ -307,8 +331,12 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
       real_ylm_u(shells_lmax_f(t.bshell, s0, s1), u[0], u[1], u[2], Y);
       const int roff = c == 0 ? 0 : g.nFA;
       const float2* z = xi + (c == 0 ? 0 : nbA);
-      if (g.row_F >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_F + roff, 0);
-      if (g.row_L >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_L + roff, 1);
+      if (g.row_F >= 0 && g.row_L >= 0) {
+        eval_shells_x2(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_F + roff, 0, g.row_L + roff, 1);
+      } else {
+        if (g.row_F >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_F + roff, 0);
+        if (g.row_L >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_L + roff, 1);
+      }
     }
   }
   if (g.row_G >= 0 || g.row_U >= 0) {
@@ -324,8 +352,12 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
       else { u = uC; rho = rC; }
       real_ylm_u(shells_lmax_f(t.ashell, s0, s1), u[0], u[1], u[2], Y);
       const float2* z = xi + nbA + nbB + (c == 0 ? 0 : na0);
-      if (g.row_G >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_G + roff, 0);
-      if (g.row_U >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_U + roff, 2);
+      if (g.row_G >= 0 && g.row_U >= 0) {
+        eval_shells_x2(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_G + roff, 0, g.row_U + roff, 2);
+      } else {
+        if (g.row_G >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_G + roff, 0);
+        if (g.row_U >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_U + roff, 2);
+      }
       int nf = 0;
       for (int s = s0; s < s1; ++s) nf += 2 * t.ashell[s].l + 1;
       roff += nf;

@@ -531,3 +531,51 @@ def test_assembly_matches_integration_on_other_grids():
     tol = {"S": 2e-4, "T": 2e-4, "V": 1e-3, "J2": 1e-4, "J3": 1e-2}
     for k, e in worst.items():
         assert e < tol[k], (k, e)
+
+
+# ---------------------------------------------------------------- convergence
+
+def test_grid_doubling_converges():
+    """Doubling the cells in mu, nu and phi moves every class by less each time (the PS rule
+    converges): |X(2N) - X(4N)| < |X(N) - X(2N)| for S, T, V and (P|Q) of H2 with the
+    config-1 shells (Section 3: errors fall as the grid grows)."""
+    job0 = synth.h2_fp64(0)
+    out = []
+    for f in (1, 2, 4):
+        spec = (6 * f, 4 * f, 2 * f, 4, 4, 4, 3)
+        job = synth.Job("h2", job0.atoms, job0.basis, job0.aux, [spec], oracle.S | oracle.T | oracle.V | oracle.J2)
+        out.append(oracle.compute(job, with_abs=False))
+    for k in ("S", "T", "V", "J2"):
+        d1 = np.abs(out[0][k] - out[1][k]).max()
+        d2 = np.abs(out[1][k] - out[2][k]).max()
+        assert d2 < 0.5 * d1, (k, d1, d2)
+
+
+def test_third_centre_split_reduces_grid_choice_spread():
+    """Refining the cells around the third centre (N_SP, Section 2.3 and Fig. 5) improves the
+    3-centre nuclear attraction: <i_A | 1/r_C | j_B> on the grid (A,B;C), refined around C
+    where 1/r_C is singular, agrees with the same integral on (A,C;B), where C is a focus and
+    the singularity is absorbed by the Jacobian, 5x better with N_SP = 3 than without the
+    split (N_SP = 1) on a coarse grid."""
+    job = synth.triatomic_oh2(0)
+    RC = np.array(job.atoms[2][1])
+    shells_A = [s for s in job.basis if s[0] == 0 and s[3] < 5][:2]
+    shells_B = [s for s in job.basis if s[0] == 1 and s[3] < 5][:2]
+
+    def spread(nsp):
+        vals = []
+        for (X, Y, Zc) in ((0, 1, 2), (0, 2, 1)):
+            g = oracle.build_grid(job.atoms, (10, 8, 6, 4, 4, 4, nsp), X, Y, Zc)
+            P, w = g["P"], g["w"]
+
+            def vals_at(shells, atom):
+                d = P - np.array(job.atoms[atom][1])
+                return oracle.sto_values(shells, np.linalg.norm(d, axis=1), d)
+
+            FA, FB = vals_at(shells_A, 0), vals_at(shells_B, 1)
+            rC = np.linalg.norm(P - RC, axis=1)
+            vals.append((FA * (w / rC)) @ FB.T)
+        return np.abs(vals[0] - vals[1]).max()
+
+    s1, s3 = spread(1), spread(3)
+    assert s3 < 0.3 * s1, (s1, s3)
