@@ -36,7 +36,7 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is pro
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400, help="timed steps (default: ~0.5 s of the default workload)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="psq", choices=["psq", "reference"])
     ap.add_argument("--workload", default="triatomic_oh2")
@@ -145,12 +145,19 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Starts sampling every 200 ms and returns once the first sample is written (so the
+        timed region that follows is covered from its start)."""
+        self.skip = 0
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
+            self.skip = sum(1 for _ in open(self.path))  # samples taken before the region
         except Exception:
             self.proc = None
 
@@ -163,7 +170,10 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         rows = []
-        for line in open(self.path):
+        lines = open(self.path).readlines()
+        # the samples inside the timed region (the last one before it if the region was shorter
+        # than the sampling period)
+        for line in lines[max(0, min(self.skip, len(lines) - 1)):]:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
                 rows.append(f)
