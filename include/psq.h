@@ -61,8 +61,11 @@ typedef struct { int n_mu, n_nu, n_phi, q_mu, q_nu, q_phi, n_sp; } psq_grid_spec
 
 typedef enum {
   PSQ_FP64 = 0,  /* plain path: every step in FP64 */
-  PSQ_MIXED = 1  /* FP64 grid, weights, potentials and accumulation; FP32 STO values;
-                    contraction on tcgen05 tensor cores with 3-piece BF16 splits */
+  PSQ_MIXED = 1  /* FP64 node tables, third-centre offsets, row constants and range sums;
+                    FP32 weights, STO values and aux potentials; contraction on tcgen05
+                    tensor cores: four 8-bit integer slices per value in BF16 under a
+                    power-of-two scale per row and 128-point window, the slice products of
+                    orders 0..3 accumulated exactly in FP32 */
 } psq_precision;
 
 enum { PSQ_S = 1, PSQ_T = 2, PSQ_V = 4, PSQ_J2 = 8, PSQ_J3 = 16, PSQ_ALL = 31 };

@@ -134,7 +134,7 @@ struct SrcEntry {
 // offW+lj.
 struct J3Src { int64_t off; int s_pair, s_aux, mode, nloc, offY, offW; };
 
-struct PointBlock { int grid; int pad; int64_t p0; };  // evaluation: 256 points of one grid
+struct PointBlock { int grid; int pad; int64_t p0; };  // evaluation: 128 points (one window) of one grid
 
 }  // namespace psq
 
