@@ -516,10 +516,10 @@ __device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)r * 128
 
 }  // namespace mma
 
-// One CTA per (panel, tile, 128-point window, 64-row group), four threads per row: thread
-// (r, qd) packs points [32 qd, 32 qd + 32) of the window (chunk qd / 2, half qd % 2) of row r;
-// the four threads of a row share the window's scale.
-__global__ void __launch_bounds__(256, 4) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
+// One CTA of 512 threads per (panel, tile, 128-point window, 64-row group), eight threads
+// per row: thread (r, e) packs points [16 (e % 4), 16 (e % 4) + 16) of chunk e / 4 of the
+// window for row r; the eight threads of a row share the window's scale.
+__global__ void __launch_bounds__(512, 3) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
                                                    int n_panels, const short2* __restrict__ rows,
                                                    const float* __restrict__ ops, uint8_t* __restrict__ packed) {
   using namespace mma;
@@ -534,11 +534,11 @@ __global__ void __launch_bounds__(256, 4) pack_kernel(const DevGrid* __restrict_
   const int64_t lj = job - pn.job_begin;
   const int t = (int)(lj / ((int64_t)pn.nwin * groups));
   const int w = (int)((lj / groups) % pn.nwin), grp = (int)(lj % groups);
-  const int r = 64 * grp + (threadIdx.x >> 2), qd = threadIdx.x & 3;
+  const int r = 64 * grp + (threadIdx.x >> 3), e8 = threadIdx.x & 7;
   const DevGrid& g = grids[pn.grid];
-  const int c = 2 * w + (qd >> 1), hh = qd & 1;
+  const int c = 2 * w + (e8 >> 2), qq = e8 & 3;
   const int row = t * pn.tr + r;
-  const int64_t k0 = 64 * (int64_t)c + 32 * hh;  // first point of this thread
+  const int64_t k0 = 64 * (int64_t)c + 16 * qq;
   const float* src = nullptr;
   const float* mul = nullptr;
   if (row < pn.nrows && c < pn.nch) {
@@ -547,43 +547,44 @@ __global__ void __launch_bounds__(256, 4) pack_kernel(const DevGrid* __restrict_
     if (q.y >= 0) mul = ops + g.op_off + (int64_t)q.y * g.ld + k0;
   }
   const int64_t left = g.K - k0;
-  float v[32];
-  if (src && left >= 32) {
+  float v[16];
+  if (src && left >= 16) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
     const float4* m4 = reinterpret_cast<const float4*>(mul);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 4; ++i) {
       float4 a = __ldg(s4 + i);
       if (mul) {
-        const float4 b = __ldg(m4 + i);
-        a.x *= b.x; a.y *= b.y; a.z *= b.z; a.w *= b.w;
+        const float4 bb = __ldg(m4 + i);
+        a.x *= bb.x; a.y *= bb.y; a.z *= bb.z; a.w *= bb.w;
       }
       v[4 * i] = a.x; v[4 * i + 1] = a.y; v[4 * i + 2] = a.z; v[4 * i + 3] = a.w;
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = (src && i < left) ? src[i] * (mul ? mul[i] : 1.0f) : 0.0f;
+    for (int i = 0; i < 16; ++i) v[i] = (src && i < left) ? src[i] * (mul ? mul[i] : 1.0f) : 0.0f;
   }
   float mx = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fabsf(v[i]));
-  const unsigned quad_mask = 0xfu << ((threadIdx.x & 31) & ~3u);
-  mx = fmaxf(mx, __shfl_xor_sync(quad_mask, mx, 1));
-  mx = fmaxf(mx, __shfl_xor_sync(quad_mask, mx, 2));
+  for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fabsf(v[i]));
+  const unsigned m8 = 0xffu << ((threadIdx.x & 31) & ~7u);
+  mx = fmaxf(mx, __shfl_xor_sync(m8, mx, 1));
+  mx = fmaxf(mx, __shfl_xor_sync(m8, mx, 2));
+  mx = fmaxf(mx, __shfl_xor_sync(m8, mx, 4));
   const int e = row_exponent(mx);
-  if (qd == 0)
+  if (e8 == 0)
     *reinterpret_cast<int*>(packed + pn.exp_off + (((int64_t)t * pn.nwin + w) * pn.tr + r) * 4) = e;
-  const int rt = min(pn.tr, pn.nrows - t * pn.tr);  // rows stored for this tile
+  const int rt = min(pn.tr, pn.nrows - t * pn.tr);
   if (c >= pn.nch || r >= rt) return;
   const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
   uint8_t* dst = packed + pn.pack_off + (int64_t)t * pn.nch * (4 * pn.tr * 128) + (int64_t)c * (4 * rt * 128);
   const int plane = rt * 128;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < 2; ++j) {
     uint4 wv[kSlices];
     slice8(v + 8 * j, sc, wv);
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(r, 4 * hh + j)) = wv[k];
+    for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(r, 2 * qq + j)) = wv[k];
   }
 }
 
@@ -1104,7 +1105,7 @@ cudaError_t prepare_kernels() {
 cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
                         const float* ops, uint8_t* packed, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
-  pack_kernel<<<(unsigned)n_jobs, 256, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
+  pack_kernel<<<(unsigned)n_jobs, 512, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
   return cudaGetLastError();
 }
 
