@@ -956,6 +956,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       const MmaBlock& b = *q.blk;
       const Panel& pa = panels[b.a_panel];
       const Panel* pb = q.formed ? nullptr : panels + b.b_panel;
+      const int rows_valid = min(kM, b.m - it.tm * kM);  // real rows of the A tile
       float H[32], L[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) { H[j] = 0.0f; L[j] = 0.0f; }
@@ -987,7 +988,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
         for (int gi = 0; gi < 2; ++gi) {
           const int gq = 2 * gi + half;  // 16-column group
-          if (gq * 16 < q.ntp) {
+          // a warp whose 32 rows are all past the tile's last real row has nothing to fold
+          if (gq * 16 < q.ntp && quad * 32 < rows_valid) {
 #pragma unroll
             for (int sub = 0; sub < 2; ++sub) {
               const int c0 = gq * 16 + 8 * sub;  // first of 8 columns
