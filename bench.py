@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work split")
+    ap.add_argument("--no-ri", action="store_true", help="skip timing the RI 4-index assembly")
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the step benchmark")
     ap.add_argument("--rates", default="20,100", help="serving: Poisson arrival rates (jobs/s)")
     ap.add_argument("--jobs", type=int, default=24, help="serving: jobs per rate")
@@ -189,6 +190,40 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ traffic record
+
+def time_ri(J2, J3, stream, reps=20):
+    """Device time of the RI 4-index assembly (eq 14) on the job's own (P|Q) and (P|ij): Cholesky
+    factor, forward solve of all pairs, then (ij|kl) for the first min(pairs, 4096) pairs
+    against each other (FP64 CUDA cores)."""
+    import torch
+    import paper_2510_15204_gb300 as P
+    n = J2.shape[0]
+    B = torch.empty((n, J3.numel() // max(n, 1)), dtype=torch.float64, device=J3.device)
+    m = B.shape[1]
+    mb = min(m, 4096)
+    eri = torch.empty((mb, mb), dtype=torch.float64, device=J3.device)
+    L = torch.empty_like(J2)
+
+    def once():
+        P.ri_factor(J2, L=L, stream=stream)
+        B.copy_(J3.reshape(n, m))
+        P.ri_solve(L, B, stream=stream)
+        P.ri_eri(B, 0, mb, 0, mb, out=eri, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            once()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = n ** 3 / 3.0 + float(n) * n * m + 2.0 * n * mb * mb
+    return {"ms": ms, "n_aux": n, "pairs": m, "eri_pairs": mb, "fp64_flop": flops, "tflops": flops / (ms / 1e3) / 1e12,
+            "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64"}
+
 
 def recorded_traffic(kernel, workload, precision):
     """DRAM bytes per launch of `kernel` from profiles/traffic.txt, if recorded for the current
@@ -382,6 +417,11 @@ def main():
     h2d, d2h = J.io_bytes(mask)
     _, (e2e_val,) = aggregate([e2e_s], [st["contractions"] * args.e2e_steps], world)
 
+    # RI 4-index assembly (eq 14) on this step's (P|Q) and (P|ij): factor, solve, all (ij|kl)
+    ri = None
+    if "J2" in out and "J3" in out and not args.no_ri:
+        ri = time_ri(out["J2"], out["J3"], stream)
+
     # roofline of the dominant kernel, timed live inside the timed region
     kind = max(prof, key=lambda k: prof[k][0])
     kms, kcount = prof[kind]
@@ -422,6 +462,7 @@ def main():
         "graph": graph,
         "autotune": tuned,
         "plain_fp64": plain,
+        "ri_4index": ri,
         "gpu_launches": st["launches"] * args.steps,
         "clocks": clk,
     }

@@ -215,6 +215,30 @@ psq_status psq_server_destroy(psq_server* server);
 /* Thread-local message describing the calling thread's last error. */
 const char* psq_last_error(void);
 
+/* RI 4-index assembly (Section 3, eq 14): (ij|kl) ~ sum_PQ (ij|P) [(PQ)^-1] (Q|kl), from the
+ * (P|Q) and (P|ij) matrices that psq_compute writes.  With the Cholesky factor (P|Q) = L L^T
+ * and B = L^-1 (P|ij), (ij|kl) = sum_R B[R][ij] B[R][kl].  FP64 throughout, on the device,
+ * asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream), on the current
+ * device.  Matrices are row-major; the pair index of (P|ij) is ij = i * n_bf + j, so its
+ * n_aux x n_bf x n_bf layout is B's n x m layout with m = n_bf^2.  The caller owns every
+ * buffer.  Errors: PSQ_ERR_ARG for negative sizes, NULL or non-8-byte-aligned pointers with
+ * nonzero sizes, or column ranges outside [0, m); PSQ_ERR_CUDA on a failed launch. */
+
+/* Cholesky factor of the symmetric positive definite n x n matrix d_J2 (its lower triangle is
+ * read): d_L (n x n; may equal d_J2) receives L, lower triangular, zeros above the diagonal.
+ * *d_info (device int) is set to 0, or to k + 1 when the k-th pivot is not positive (the
+ * matrix is not positive definite; d_L is then undefined).  Read it after the stream. */
+psq_status psq_ri_factor(int n, const double* d_J2, double* d_L, int* d_info, void* stream);
+
+/* Forward substitution in place: d_B (n x m) <- L^-1 d_B, L from psq_ri_factor. */
+psq_status psq_ri_solve(int n, int64_t m, const double* d_L, double* d_B, void* stream);
+
+/* A block of 4-index integrals: d_out[c][d] = sum_R B[R][c0 + c] B[R][d0 + d] for
+ * 0 <= c < nc, 0 <= d < nd (row-major nc x nd), B (n x m) from psq_ri_solve: with ij = c0 + c
+ * and kl = d0 + d, the RI value of (ij|kl). */
+psq_status psq_ri_eri(int n, int64_t m, const double* d_B, int64_t c0, int64_t nc, int64_t d0, int64_t nd,
+                      double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

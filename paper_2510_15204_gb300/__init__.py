@@ -76,6 +76,10 @@ SIGNATURES = [
     ("psq_server_wait", _I, [_VP, ctypes.c_uint64, _D]),
     ("psq_server_destroy", _I, [_VP]),
     ("psq_last_error", ctypes.c_char_p, []),
+    ("psq_ri_factor", _I, [_I, _VP, _VP, _VP, _VP]),
+    ("psq_ri_solve", _I, [_I, ctypes.c_int64, _VP, _VP, _VP]),
+    ("psq_ri_eri", _I, [_I, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                        _VP, _VP]),
 ]
 
 
@@ -104,6 +108,47 @@ def _stream_ptr(stream):
         import torch
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_f64(t, name):
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ri_factor(J2, L=None, stream=None):
+    """Cholesky factor of the RI metric (P|Q) (eq 14's (PQ)^-1 is L^-T L^-1): returns (L, info),
+    info a 1-element int32 CUDA tensor, 0 or k + 1 for a non-positive k-th pivot.  Asynchronous."""
+    import torch
+    n = J2.shape[0]
+    if J2.shape != (n, n):
+        raise ValueError("J2 must be square")
+    L = torch.empty_like(J2) if L is None else L
+    info = torch.empty(1, dtype=torch.int32, device=J2.device)
+    _check(lib().psq_ri_factor(n, _dev_f64(J2, "J2"), _dev_f64(L, "L"), ctypes.c_void_p(info.data_ptr()),
+                               _stream_ptr(stream)))
+    return L, info
+
+
+def ri_solve(L, B, stream=None):
+    """B <- L^-1 B in place (B: n_aux rows; (P|ij) reshaped to n_aux x n_bf^2).  Asynchronous."""
+    n = L.shape[0]
+    m = B.numel() // n if n else 0
+    if B.shape[0] != n:
+        raise ValueError("B must have n rows")
+    _check(lib().psq_ri_solve(n, m, _dev_f64(L, "L"), _dev_f64(B, "B"), _stream_ptr(stream)))
+    return B
+
+
+def ri_eri(B, c0, nc, d0, nd, out=None, stream=None):
+    """Block of RI 4-index integrals (eq 14): out[c][d] = (ij|kl) for ij = c0 + c, kl = d0 + d
+    (pair index i * n_bf + j), B from ri_solve.  Asynchronous."""
+    import torch
+    n = B.shape[0]
+    m = B.numel() // n if n else 0
+    out = torch.empty((nc, nd), dtype=torch.float64, device=B.device) if out is None else out
+    _check(lib().psq_ri_eri(n, m, _dev_f64(B, "B"), c0, nc, d0, nd, _dev_f64(out, "out"), _stream_ptr(stream)))
+    return out
 
 
 class Context:
