@@ -224,6 +224,29 @@ def fivez_triatomic(seed: int = 0, spec=(30, 25, 16, 5, 4, 4, 3), mask: int = AL
     return Job("fivez_triatomic", atoms, basis, aux, [tuple(spec)], mask, {"seed": seed})
 
 
+def paper_job(molecule: str, spec=(26, 20, 8, 4, 4, 4, 3), mask: int = ALL) -> Job:
+    """A molecule of the paper's Table S2 in its TZ basis (Table S1), aux by the combinatorial
+    recipe of Section 3 with the per-l counts of ``paper_tables.AUX_COUNTS`` (unprinted in
+    the paper).  Default grid: the smallest of Table S3 (26 / 20 / 8, Q 4, N_SP 3)."""
+    from . import paper_tables as pt
+    atoms = pt.atoms_of(molecule)
+    basis = pt.basis_of(molecule)
+    aux = []
+    for a, (e, _) in enumerate(pt.GEOMETRIES[molecule]):
+        aux += combinatorial_aux(a, basis, pt.AUX_COUNTS[e])
+    return Job(molecule.lower() + "_tz", atoms, basis, aux, [tuple(spec)], mask, {"molecule": molecule})
+
+
+def clf_tz(seed: int = 0, spec=(26, 20, 8, 4, 4, 4, 3), mask: int = ALL) -> Job:
+    """ClF in the paper's TZ basis, Table S2 geometry (Figs. 3-4); seed unused."""
+    return paper_job("ClF", spec, mask)
+
+
+def of2_tz(seed: int = 0, spec=(26, 20, 8, 4, 4, 4, 3), mask: int = ALL) -> Job:
+    """OF2 in the paper's TZ basis, Table S2 geometry (Figs. 3-5); seed unused."""
+    return paper_job("OF2", spec, mask)
+
+
 def _check_min_distance(atoms, dmin):
     p = np.array([a[1] for a in atoms])
     for i in range(len(p)):
