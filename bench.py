@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work split")
     ap.add_argument("--no-ri", action="store_true", help="skip timing the RI 4-index assembly")
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the step benchmark")
+    ap.add_argument("--scan", action="store_true", help="Fig. 6 displacement scans through the serving loop")
     ap.add_argument("--rates", default="20,100", help="serving: Poisson arrival rates (jobs/s)")
     ap.add_argument("--jobs", type=int, default=24, help="serving: jobs per rate")
     ap.add_argument("--baseline-jobs", type=int, default=6, help="serving: jobs timed on the per-job FP64 path")
@@ -313,6 +314,55 @@ def serve_main(args):
     return 0
 
 
+def scan_main(args):
+    """The Fig. 6 displacement scans as a throughput workload: every point of every path is
+    its own diatomic (P|Q) job, all submitted at once to the continuous-batching server (mixed
+    precision); per-job plain FP64 launches on the first jobs beside it, and the largest
+    deviation of the served (P|Q) path values from those FP64 values."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2510_15204_gb300 import build as B
+    B.build()
+    import paper_2510_15204_gb300 as P
+    torch.cuda.set_device(0)
+    ctx = P.Context(0)
+    mask = P.J2
+    scan = synth.displacement_scan()
+    jobs = [P.Job.from_synth(ctx, j, P.MIXED) for _, j in scan]
+    outs = [{k: torch.empty(sh, dtype=torch.float64).pin_memory() for k, sh in J.out_shapes(mask).items()}
+            for J in jobs]
+    for J in jobs:
+        J.workspace_bytes(mask)  # plan up front (host work, not serving latency)
+    server = P.Server(ctx, arena_bytes=int(torch.cuda.mem_get_info()[0] * 0.5), max_inflight=8)
+    t0 = time.perf_counter()
+    tickets = [server.submit(J, mask, o) for J, o in zip(jobs, outs)]
+    lat = [server.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    server.close()
+    n_fp64 = min(args.baseline_jobs * 50, len(jobs))
+    dev, t_gpu = 0.0, 0.0
+    for (meta, j), o in zip(scan[:n_fp64], outs[:n_fp64]):
+        J = P.Job.from_synth(ctx, j, P.FP64)
+        ws, out = J.alloc(mask)
+        host = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in out.items()}
+        t1 = time.perf_counter()
+        J.compute_host(mask, ws, out, host)
+        t_gpu += time.perf_counter() - t1
+        r, c = meta[4], meta[5]
+        dev = max(dev, abs(float(o["J2"][r, c]) - float(host["J2"][r, c])))
+    res = {"metric": "Fig. 6 displacement scans through the serving loop", "unit": "jobs/s", "higher_is_better": True,
+           "data": "synthetic", "n_gpus": 1,
+           "config": {"workload": "displacement_scan", "paths": len(synth.SCAN_PAIRS) * 16, "points_per_path": 51,
+                      "pairs_l": synth.SCAN_PAIRS, "grid": list(scan[0][1].specs[0]), "precision": "mixed"},
+           "jobs": len(jobs), "value": len(jobs) / wall, "wall_s": wall,
+           "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+           "fp64_per_job": {"jobs": n_fp64, "jobs_per_s": n_fp64 / t_gpu},
+           "max_abs_dev_vs_fp64": dev}
+    print(json.dumps(res))
+    return 0
+
+
 # ------------------------------------------------------------------------------ GPU arm
 
 def main():
@@ -321,6 +371,8 @@ def main():
         return reference_arm(args)
     if args.serve:
         return serve_main(args)
+    if args.scan:
+        return scan_main(args)
     rank, world, local = dist_env()
     import torch
     import synth

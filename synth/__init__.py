@@ -247,6 +247,44 @@ def of2_tz(seed: int = 0, spec=(26, 20, 8, 4, 4, 4, 3), mask: int = ALL) -> Job:
     return paper_job("OF2", spec, mask)
 
 
+SCAN_PAIRS = ((0, 0), (1, 1), (2, 2), (1, 3), (3, 3), (3, 5))
+
+
+def scan_directions(k: int = 16):
+    """k unit vectors spread over the sphere (Fibonacci lattice): the displacement directions
+    of the Fig. 6 scans (the paper's 16 directions are not listed)."""
+    g = math.pi * (3.0 - math.sqrt(5.0))
+    out = []
+    for i in range(k):
+        z = 1.0 - (2 * i + 1) / k
+        r = math.sqrt(1.0 - z * z)
+        out.append((r * math.cos(g * i), r * math.sin(g * i), z))
+    return out
+
+
+def displacement_scan(pairs=SCAN_PAIRS, directions=None, distances=None, spec=(80, 70, 50, 4, 4, 4, 3),
+                      mask: int = J2):
+    """The Fig. 6 workload: one aux function of angular momentum l1 (zeta = 1, n = l1 + 1) at
+    the origin, one of l2 at R d for each direction d and distance R (1.0 to 6.0 bohr in steps
+    of 0.1), on the paper's large PS grid (80 / 70 / 50, Q 4); (P|Q) of their m = 0 components
+    along each path.  Below about 1 bohr the truncated spheroid of eq 17 (mu_max = C1
+    atanh(N/(N+1)), C1 = 2.3 a^(1/4)) no longer holds zeta = 1 functions.  Each point is its
+    own diatomic job (a 1s basis function, zeta = 1, on each centre).  Returns [(meta, Job)],
+    meta = (l1, l2, direction index, R, row of P, column of Q in (P|Q))."""
+    directions = scan_directions() if directions is None else directions
+    distances = [round(1.0 + 0.1 * i, 10) for i in range(51)] if distances is None else distances
+    out = []
+    for (l1, l2) in pairs:
+        for di, d in enumerate(directions):
+            for R in distances:
+                atoms = [(1, (0.0, 0.0, 0.0)), (1, (R * d[0], R * d[1], R * d[2]))]
+                basis = [(0, 1, 0, 1.0), (1, 1, 0, 1.0)]
+                aux = [(0, l1 + 1, l1, 1.0), (1, l2 + 1, l2, 1.0)]
+                job = Job("scan", atoms, basis, aux, [tuple(spec)], mask, {"R": R, "dir": di})
+                out.append(((l1, l2, di, R, l1, 2 * l1 + 1 + l2), job))
+    return out
+
+
 def _check_min_distance(atoms, dmin):
     p = np.array([a[1] for a in atoms])
     for i in range(len(p)):
