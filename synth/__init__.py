@@ -224,17 +224,20 @@ def fivez_triatomic(seed: int = 0, spec=(30, 25, 16, 5, 4, 4, 3), mask: int = AL
     return Job("fivez_triatomic", atoms, basis, aux, [tuple(spec)], mask, {"seed": seed})
 
 
-def paper_job(molecule: str, spec=(26, 20, 8, 4, 4, 4, 3), mask: int = ALL) -> Job:
-    """A molecule of the paper's Table S2 in its TZ basis (Table S1), aux by the combinatorial
-    recipe of Section 3 with the per-l counts of ``paper_tables.AUX_COUNTS`` (unprinted in
-    the paper).  Default grid: the smallest of Table S3 (26 / 20 / 8, Q 4, N_SP 3)."""
+def paper_job(molecule: str, spec=(26, 20, 8, 4, 4, 4, 3), mask: int = ALL, basis: str = "TZ") -> Job:
+    """A molecule of the paper's Table S2 in one of its Slater bases (Table S1: "TZ", "QZ",
+    "5Z"), aux by the combinatorial recipe of Section 3 with the per-l counts of
+    ``paper_tables.AUX_COUNTS`` (TZ) / ``AUX_COUNTS_HIGH`` (QZ, 5Z), a reading: the paper does
+    not print them.  Default grid: the smallest of Table S3 (26 / 20 / 8, Q 4, N_SP 3)."""
     from . import paper_tables as pt
     atoms = pt.atoms_of(molecule)
-    basis = pt.basis_of(molecule)
+    shells = pt.basis_of(molecule, basis)
+    counts = pt.AUX_COUNTS if basis == "TZ" else pt.AUX_COUNTS_HIGH
     aux = []
     for a, (e, _) in enumerate(pt.GEOMETRIES[molecule]):
-        aux += combinatorial_aux(a, basis, pt.AUX_COUNTS[e])
-    return Job(molecule.lower() + "_tz", atoms, basis, aux, [tuple(spec)], mask, {"molecule": molecule})
+        aux += combinatorial_aux(a, shells, counts[e])
+    name = molecule.lower() + "_" + basis.lower()
+    return Job(name, atoms, shells, aux, [tuple(spec)], mask, {"molecule": molecule, "basis": basis})
 
 
 def clf_tz(seed: int = 0, spec=(26, 20, 8, 4, 4, 4, 3), mask: int = ALL) -> Job:

@@ -10,13 +10,14 @@ import synth
 from synth import paper_tables as pt
 
 
+@pytest.mark.parametrize("col", ["TZ", "QZ", "5Z"])
 @pytest.mark.parametrize("el", sorted(pt.TZ))
-def test_tz_exponents_are_even_tempered(el):
-    for l, zs in pt.TZ[el].items():
+def test_exponents_are_even_tempered(col, el):
+    for l, zs in pt.TABLES[col][el].items():
         if len(zs) < 3:
             continue
         r = np.array(zs[:-1]) / np.array(zs[1:])
-        assert np.abs(r / r.mean() - 1).max() < 2e-3, (el, l, r)
+        assert np.abs(r / r.mean() - 1).max() < 2e-3, (col, el, l, r)
 
 
 def _dist(mol, i, j):
@@ -45,3 +46,13 @@ def test_paper_jobs_sizes():
     assert max(s[2] for s in j.aux) == 4  # aux up to g (Section 4)
     assert abs(j.atoms[0][1][2] - 1.628 * pt.ANGSTROM) < 1e-12
     assert synth.of2_tz().n_bf == 75
+
+
+def test_qz_5z_sizes():
+    """Shell counts per column as Table S1 lists them (e.g. C: QZ 8s4p3d1f, 5Z 9s5p4d2f)."""
+    count = lambda col, el: tuple(len(pt.TABLES[col][el].get(l, [])) for l in range(4))
+    assert count("QZ", "C") == (8, 4, 3, 1) and count("5Z", "C") == (9, 5, 4, 2)
+    assert count("QZ", "Cl") == (12, 8, 3, 1) and count("5Z", "Cl") == (12, 10, 4, 2)
+    assert count("QZ", "H") == (4, 3, 1, 0) and count("5Z", "H") == (5, 4, 2, 0)
+    j = synth.paper_job("CO", basis="5Z")
+    assert j.n_bf == 2 * (9 + 15 + 20 + 14) and max(s[2] for s in j.aux) == 6
