@@ -332,6 +332,8 @@ psq_status build_grid(const psq_job* j, GridKey key, DevGrid& g, std::vector<dou
   const int64_t q3 = (int64_t)sp.q_mu * sp.q_nu * sp.q_phi;
   g.K_reg = (int64_t)sp.n_mu * sp.n_nu * sp.n_phi * q3;
   g.K = g.K_reg + (int64_t)g.n_touch * sp.n_sp * sp.n_sp * sp.n_sp * q3;
+  if (g.K > ((int64_t)1 << 31) - 256)  // point indices are 32-bit in the kernels
+    return fail(PSQ_ERR_UNSUPPORTED, "a grid with its split cells has more than 2^31 - 256 points");
   return PSQ_OK;
 }
 

@@ -258,26 +258,28 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
                                                          float* __restrict__ ops) {
   const PointBlock pb = t.pblocks[blockIdx.x];
   const DevGrid& g = t.grids[pb.grid];
-  const int64_t p = pb.p0 + threadIdx.x;
+  const int p = (int)pb.p0 + (int)threadIdx.x;  // K < 2^31 - 256 (the planner checks)
   if (p >= g.K) return;
   const int q3 = g.q_mu * g.q_nu * g.q_phi;
   int ri, rj, rk;
   bool dead = false;
-  int64_t pr;
+  int pr;
   if (p < g.K_reg) {
-    const int64_t cell = p / q3;
+    const int cell = p / q3;
     pr = p - cell * q3;
-    rk = (int)(cell % g.n_phi);
-    rj = (int)((cell / g.n_phi) % g.n_nu);
-    ri = (int)(cell / ((int64_t)g.n_phi * g.n_nu));
+    const int cnp = cell / g.n_phi;
+    rk = cell - cnp * g.n_phi;
+    ri = cnp / g.n_nu;
+    rj = cnp - ri * g.n_nu;
     if (g.n_touch > 0 && ri >= g.t_mu0 && ri <= g.t_mu1 && rj >= g.t_nu0 && rj <= g.t_nu1 &&
         (g.t_phi_all || rk == 0 || rk == g.n_phi - 1))
       dead = true;
   } else {
-    const int64_t s = (p - g.K_reg) / q3;
-    pr = (p - g.K_reg) - s * q3;
+    const int pe = p - (int)g.K_reg;
+    const int s = pe / q3;
+    pr = pe - s * q3;
     const int ns = g.n_sp, ns3 = ns * ns * ns;
-    const int tc = (int)(s / ns3), sub = (int)(s % ns3);
+    const int tc = s / ns3, sub = s - tc * ns3;
     const int ntp = g.nt_phi, nnu = g.nt_nu;
     const int ti = tc / (nnu * ntp), tj = (tc / ntp) % nnu, tk = tc % ntp;
     const int si = sub / (ns * ns), sj = (sub / ns) % ns, sk = sub % ns;
@@ -285,9 +287,10 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
     rj = g.n_nu + tj * ns + sj;
     rk = g.n_phi + tk * ns + sk;
   }
-  const int qi = (int)(pr / (g.q_nu * g.q_phi));
-  const int qj = (int)((pr / g.q_phi) % g.q_nu);
-  const int qk = (int)(pr % g.q_phi);
+  const int qnp = pr / g.q_phi;
+  const int qk = pr - qnp * g.q_phi;
+  const int qi = qnp / g.q_nu;
+  const int qj = qnp - qi * g.q_nu;
   const int nmu = (g.n_mu + g.nt_mu * g.n_sp) * g.q_mu;
   const int nnu = (g.n_nu + g.nt_nu * g.n_sp) * g.q_nu;
   const NodeEntry Mu = tab[g.nt_off + ri * g.q_mu + qi];
@@ -530,10 +533,10 @@ __global__ void __launch_bounds__(512, 3) pack_kernel(const DevGrid* __restrict_
     if (panels[mid].job_begin <= job) lo = mid; else hi = mid;
   }
   const Panel pn = panels[lo];
-  const int groups = pn.tr / 64;
-  const int64_t lj = job - pn.job_begin;
-  const int t = (int)(lj / ((int64_t)pn.nwin * groups));
-  const int w = (int)((lj / groups) % pn.nwin), grp = (int)(lj % groups);
+  const int gsh = pn.tr >> 7;  // 64-row groups per tile: 1 (tr 64) or 2 (tr 128)
+  const int lj = (int)(job - pn.job_begin);  // jobs of one panel < 2^31 (one launch's grid)
+  const int tw = lj >> gsh, grp = lj & gsh;
+  const int t = tw / pn.nwin, w = tw - t * pn.nwin;
   const int r = 64 * grp + (threadIdx.x >> 3), e8 = threadIdx.x & 7;
   const DevGrid& g = grids[pn.grid];
   const int c = 2 * w + (e8 >> 2), qq = e8 & 3;
