@@ -382,4 +382,6 @@ WORKLOADS = {
     "c3h6": c3h6,
     "fivez_diatomic": fivez_diatomic,
     "fivez_triatomic": fivez_triatomic,
+    "clf_tz": clf_tz,
+    "of2_tz": of2_tz,
 }
