@@ -163,3 +163,21 @@ def test_autotune_needs_a_device(P, ctx):
     ptrs = (ctypes.c_void_p * 5)()
     st = P.lib().psq_job_autotune(J.handle, oracle.ALL, None, 0, ptrs, None, None, None)
     assert st == 1  # PSQ_ERR_ARG: planning-only context
+
+
+def test_ri_entry_points_validate_arguments_without_a_gpu(P):
+    """psq_ri_* refuse bad sizes, ranges and pointers before touching the device."""
+    import ctypes
+    L = P.lib()
+    dummy = ctypes.c_void_p(64)  # never dereferenced: every call below fails its checks first
+    info = ctypes.c_void_p(64)
+    assert L.psq_ri_factor(-1, dummy, dummy, info, None) == 1
+    assert L.psq_ri_factor(4, None, dummy, info, None) == 1
+    assert L.psq_ri_factor(4, dummy, dummy, None, None) == 1
+    assert L.psq_ri_factor(4, ctypes.c_void_p(65), dummy, info, None) == 1  # misaligned
+    assert L.psq_ri_solve(-2, 5, dummy, dummy, None) == 1
+    assert L.psq_ri_solve(3, 5, None, dummy, None) == 1
+    assert L.psq_ri_solve(0, 5, None, None, None) == 0  # nothing to do
+    assert L.psq_ri_eri(3, 10, dummy, 8, 5, 0, 2, dummy, None) == 1  # c0 + nc > m
+    assert L.psq_ri_eri(3, 10, dummy, 0, 2, -1, 2, dummy, None) == 1
+    assert L.psq_ri_eri(3, 10, dummy, 0, 0, 0, 4, None, None) == 0  # empty block
