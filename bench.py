@@ -195,7 +195,7 @@ class ClockSampler:
 def time_ri(J2, J3, stream, reps=20):
     """Device time of the RI 4-index assembly (eq 14) on the job's own (P|Q) and (P|ij): Cholesky
     factor, forward solve of all pairs, then (ij|kl) for the first min(pairs, 4096) pairs
-    against each other (FP64 CUDA cores)."""
+    against each other (FP64 CUDA cores), replayed from a captured CUDA graph."""
     import torch
     import paper_2510_15204_gb300 as P
     n = J2.shape[0]
@@ -214,10 +214,17 @@ def time_ri(J2, J3, stream, reps=20):
     with torch.cuda.stream(stream):
         for _ in range(3):
             once()
+        torch.cuda.synchronize()
+        # replayed from a CUDA graph: the ~20 small launches of a small job would otherwise
+        # wait on the host between them
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            once()
+        graph.replay()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            once()
+            graph.replay()
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps

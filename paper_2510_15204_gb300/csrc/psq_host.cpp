@@ -761,8 +761,20 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       const int64_t c0 = 2LL * it.chunk * mb.win_per;
       return std::max<int64_t>(0, std::min<int64_t>(nch, c0 + 2LL * mb.win_per) - c0);
     };
+    // Items by estimated cost, largest first (a window of a formed pair tile costs about twice
+    // a packed one: the producers' slicing), then dealt to the CTAs in snake order (the
+    // kernel's CTA b takes items b, b + n_ctas, ...; every other round is reversed), so that
+    // the static round-robin ends evenly.
+    auto item_cost = [&](const GemmItem& it) {
+      return (double)item_chunks(it) * (P.mblocks[it.block].b_panel < 0 ? 2.0 : 1.0);
+    };
     std::stable_sort(P.mitems.begin(), P.mitems.end(),
-                     [&](const GemmItem& x, const GemmItem& y) { return item_chunks(x) > item_chunks(y); });
+                     [&](const GemmItem& x, const GemmItem& y) { return item_cost(x) > item_cost(y); });
+    {
+      const size_t R = (size_t)std::min<int64_t>((int64_t)P.mitems.size(), j->ctx->sm_count);
+      for (size_t r0 = R; r0 < P.mitems.size(); r0 += 2 * R)
+        std::reverse(P.mitems.begin() + r0, P.mitems.begin() + std::min(P.mitems.size(), r0 + R));
+    }
     // issued tensor work: per 64-point chunk of an item, the slice products of orders 0..3
     // (10 of 128 x 64 x 64, issued as four MMAs of N = 256, 192, 128, 64)
     for (const GemmItem& it : P.mitems) P.issued_flops += (double)item_chunks(it) * 10.0 * 2.0 * 128.0 * 64.0 * 64.0;
