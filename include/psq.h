@@ -102,8 +102,8 @@ psq_status psq_job_stats(const psq_job* job, unsigned mask, int* n_grids, int64_
                          double* contractions, int* launches);
 
 /* Autotuning (the batched launch's work split; no paper counterpart).  Plans mask with each
- * candidate work split (PSQ_MIXED: 4, 8, 16 or 32 contraction work items per SM; PSQ_FP64: 2,
- * 4, 8 or 16 waves of CTAs per SM), runs each candidate that fits ws_bytes once to warm up
+ * candidate work split (PSQ_MIXED: 2, 4, 6, 8, 16 or 32 contraction work items per SM;
+ * PSQ_FP64: 2, 4, 8 or 16 waves of CTAs per SM), runs each candidate that fits ws_bytes once to warm up
  * and three times under CUDA events on stream, keeps the fastest as the job's plan for mask
  * (later psq_compute / psq_compute_graph / psq_job_workspace calls use it; graphs captured
  * before are dropped) and returns its split and mean milliseconds (either pointer may be

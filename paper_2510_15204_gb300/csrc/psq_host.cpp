@@ -1351,11 +1351,11 @@ psq_status psq_job_autotune(psq_job* job, unsigned mask, void* d_workspace, size
     if ((mask >> c) & 1 && !d_out[c]) return fail(PSQ_ERR_ARG, "output %d is NULL", c);
   if (!d_workspace || (uintptr_t)d_workspace % 256) return fail(PSQ_ERR_ARG, "workspace NULL or not 256-byte aligned");
   // candidates: work items per SM (mixed) or 8-CTA waves per SM (FP64)
-  static const int kMixed[] = {4, 8, 16, 32};
+  static const int kMixed[] = {2, 4, 6, 8, 16, 32};
   static const int kFp64[] = {2, 4, 8, 16};
   const bool mixed = job->prec == PSQ_MIXED;
   const int* cand = mixed ? kMixed : kFp64;
-  const int n_cand = 4;
+  const int n_cand = mixed ? 6 : 4;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
