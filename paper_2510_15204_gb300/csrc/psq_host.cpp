@@ -139,6 +139,9 @@ struct Plan {
   std::vector<Panel> panels;
   std::vector<PairTile> ptiles;
   int64_t n_pack_jobs = 0, pack_bytes = 0;
+  std::vector<int> cta_begin;  // contraction: CTA b takes items [cta_begin[b], cta_begin[b + 1])
+  int n_ctas = 0;
+  size_t o_cb = 0;
   size_t o_mb = 0, o_mi = 0, o_pn = 0, o_pt = 0, nodes_off = 0, o_xi = 0, o_rc = 0, pack_off = 0;
   std::vector<float2> xi;    // per grid: (hi, lo) scale turning rho into x = zeta r, per shell
   std::vector<double> rowc;  // per grid: FP64 constant of every operand row
@@ -761,19 +764,33 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       const int64_t c0 = 2LL * it.chunk * mb.win_per;
       return std::max<int64_t>(0, std::min<int64_t>(nch, c0 + 2LL * mb.win_per) - c0);
     };
-    // Items by estimated cost, largest first (a window of a formed pair tile costs about twice
-    // a packed one: the producers' slicing), then dealt to the CTAs in snake order (the
-    // kernel's CTA b takes items b, b + n_ctas, ...; every other round is reversed), so that
-    // the static round-robin ends evenly.
+    // Items by estimated cost (chunks; a formed pair tile's window counts twice: its
+    // producers' slicing), largest first, each given to the persistent CTA with the least
+    // cost so far (LPT); a CTA takes its items largest first.
     auto item_cost = [&](const GemmItem& it) {
       return (double)item_chunks(it) * (P.mblocks[it.block].b_panel < 0 ? 2.0 : 1.0);
     };
     std::stable_sort(P.mitems.begin(), P.mitems.end(),
                      [&](const GemmItem& x, const GemmItem& y) { return item_cost(x) > item_cost(y); });
+    P.n_ctas = (int)std::min<int64_t>((int64_t)P.mitems.size(), j->ctx->sm_count);
     {
-      const size_t R = (size_t)std::min<int64_t>((int64_t)P.mitems.size(), j->ctx->sm_count);
-      for (size_t r0 = R; r0 < P.mitems.size(); r0 += 2 * R)
-        std::reverse(P.mitems.begin() + r0, P.mitems.begin() + std::min(P.mitems.size(), r0 + R));
+      std::vector<std::vector<GemmItem>> per(P.n_ctas);
+      std::vector<std::pair<double, int>> heap;  // (cost so far, CTA), min-heap
+      for (int b = 0; b < P.n_ctas; ++b) heap.push_back({0.0, b});
+      auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x > y; };
+      std::make_heap(heap.begin(), heap.end(), cmp);
+      for (const GemmItem& it : P.mitems) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        per[heap.back().second].push_back(it);
+        heap.back().first += item_cost(it);
+        std::push_heap(heap.begin(), heap.end(), cmp);
+      }
+      P.mitems.clear();
+      P.cta_begin.assign(1, 0);
+      for (auto& v : per) {
+        P.mitems.insert(P.mitems.end(), v.begin(), v.end());
+        P.cta_begin.push_back((int)P.mitems.size());
+      }
     }
     // issued tensor work: per 64-point chunk of an item, the slice products of orders 0..3
     // (10 of 128 x 64 x 64, issued as four MMAs of N = 256, 192, 128, 64)
@@ -910,6 +927,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   P.o_j3 = sec(sizeof(J3Src) * P.j3.size());
   P.o_mb = sec(sizeof(MmaBlock) * P.mblocks.size());
   P.o_mi = sec(sizeof(GemmItem) * P.mitems.size());
+  P.o_cb = sec(sizeof(int) * P.cta_begin.size());
   P.o_pn = sec(sizeof(Panel) * P.panels.size());
   P.o_pt = sec(sizeof(PairTile) * P.ptiles.size());
   P.o_status = sec(sizeof(int) * 4);
@@ -967,6 +985,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   put(P.o_j3, P.j3.data(), sizeof(J3Src) * P.j3.size());
   put(P.o_mb, P.mblocks.data(), sizeof(MmaBlock) * P.mblocks.size());
   put(P.o_mi, P.mitems.data(), sizeof(GemmItem) * P.mitems.size());
+  put(P.o_cb, P.cta_begin.data(), sizeof(int) * P.cta_begin.size());
   put(P.o_pn, P.panels.data(), sizeof(Panel) * P.panels.size());
   put(P.o_pt, P.ptiles.data(), sizeof(PairTile) * P.ptiles.size());
   put(P.o_xi, P.xi.data(), sizeof(float2) * P.xi.size());
@@ -1297,9 +1316,8 @@ psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_ou
     CUDA_TRY(launch_pack(t.grids, (const Panel*)(ws + P->o_pn), (int)P->panels.size(), P->n_pack_jobs, t.pairs, ops,
                          packed, s));
     CUDA_TRY(mark(job, 2, s));
-    const int n_items = (int)P->mitems.size();
-    CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi), n_items,
-                                std::min(n_items, job->ctx->sm_count), (const Panel*)(ws + P->o_pn),
+    CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
+                                (const int*)(ws + P->o_cb), P->n_ctas, (const Panel*)(ws + P->o_pn),
                                 (const PairTile*)(ws + P->o_pt), ops, packed, (float2*)part,
                                 (int*)(ws + P->o_status), s));
     CUDA_TRY(mark(job, 3, s));

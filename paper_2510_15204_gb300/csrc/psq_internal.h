@@ -174,9 +174,10 @@ size_t ws_smem_bytes();
 cudaError_t prepare_kernels();  // per-device kernel attributes (context creation)
 cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
                         const float* ops, uint8_t* packed, cudaStream_t s);
-cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                               int n_ctas, const Panel* panels, const PairTile* ptiles, const float* ops,
-                               const uint8_t* packed, float2* part, int* status, cudaStream_t s);
+// CTA b of the persistent contraction works through items [cta_begin[b], cta_begin[b + 1]).
+cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items,
+                               const int* cta_begin, int n_ctas, const Panel* panels, const PairTile* ptiles,
+                               const float* ops, const uint8_t* packed, float2* part, int* status, cudaStream_t s);
 cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
                                 int64_t n_elems, const short2* rows, const double* rowc, const float2* part,
                                 double* res, cudaStream_t s);

@@ -721,7 +721,8 @@ __device__ __forceinline__ bool aborted(Smem& sm) { return *(volatile int*)&sm.a
 
 __global__ void __launch_bounds__(ws::kThreads, 1)
     contract_ws_kernel(const DevGrid* __restrict__ grids, const MmaBlock* __restrict__ blocks,
-                       const GemmItem* __restrict__ items, int n_items, const Panel* __restrict__ panels,
+                       const GemmItem* __restrict__ items, const int* __restrict__ cta_begin,
+                       const Panel* __restrict__ panels,
                        const PairTile* __restrict__ ptiles, const float* __restrict__ ops,
                        const uint8_t* __restrict__ packed, float2* __restrict__ part, int* __restrict__ status) {
   using namespace mma;
@@ -758,7 +759,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     // ------------------------------------------------------------------ loader
     bool run = true;                 // warp-uniform
     int last_a = -1, last_raw = -1;  // last issued chunk / formed window (for the drain)
-    for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
+    for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
       const MmaBlock& b = *q.blk;
@@ -822,7 +823,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const int g = lane & 7;
     const unsigned col_mask = 0xffu << (lane & 24);
     bool run = true;  // warp-uniform
-    for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
+    for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
       if (!q.formed) {
@@ -929,7 +930,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
   } else if (warp == ws::kMmaWarp) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
-      for (int ii = blockIdx.x; ii < n_items && !ws::aborted(sm); ii += gridDim.x) {
+      for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && !ws::aborted(sm); ++ii) {
         const GemmItem it = items[ii];
         const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
         bool ok = true;
@@ -978,7 +979,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const int half = ew >> 2;              // 16-column groups gq with gq % 2 == half
     const int row_in_tile = quad * 32 + lane;
     bool run = true;  // warp-uniform
-    for (int ii = blockIdx.x; ii < n_items && run; ii += gridDim.x) {
+    for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
       const MmaBlock& b = *q.blk;
@@ -1139,11 +1140,11 @@ cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels,
   return cudaGetLastError();
 }
 
-cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items, int n_items,
-                               int n_ctas, const Panel* panels, const PairTile* ptiles, const float* ops,
-                               const uint8_t* packed, float2* part, int* status, cudaStream_t s) {
-  if (n_items == 0) return cudaSuccess;
-  contract_ws_kernel<<<n_ctas, ws::kThreads, ws_smem_bytes(), s>>>(grids, blocks, items, n_items, panels, ptiles, ops,
+cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items,
+                               const int* cta_begin, int n_ctas, const Panel* panels, const PairTile* ptiles,
+                               const float* ops, const uint8_t* packed, float2* part, int* status, cudaStream_t s) {
+  if (n_ctas == 0) return cudaSuccess;
+  contract_ws_kernel<<<n_ctas, ws::kThreads, ws_smem_bytes(), s>>>(grids, blocks, items, cta_begin, panels, ptiles, ops,
                                                                    packed, part, status);
   return cudaGetLastError();
 }
