@@ -16,8 +16,10 @@ method written plainly in numpy FP64) on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -205,8 +207,11 @@ def time_ri(J2, J3, stream, reps=20):
     eri = torch.empty((mb, mb), dtype=torch.float64, device=J3.device)
     L = torch.empty_like(J2)
 
+    info_box = []
+
     def once():
-        P.ri_factor(J2, L=L, stream=stream)
+        _, info = P.ri_factor(J2, L=L, stream=stream)
+        info_box.append(info)
         B.copy_(J3.reshape(n, m))
         P.ri_solve(L, B, stream=stream)
         P.ri_eri(B, 0, mb, 0, mb, out=eri, stream=stream)
@@ -229,8 +234,36 @@ def time_ri(J2, J3, stream, reps=20):
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     flops = n ** 3 / 3.0 + float(n) * n * m + 2.0 * n * mb * mb
-    return {"ms": ms, "n_aux": n, "pairs": m, "eri_pairs": mb, "fp64_flop": flops, "tflops": flops / (ms / 1e3) / 1e12,
-            "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64"}
+
+    # the (ij|kl) block alone: FP64 CUDA cores against the tensor-core (8-bit slice) product
+    need = ctypes.c_size_t()
+    P.lib().psq_ri_eri_mixed_workspace(n, mb, mb, ctypes.byref(need))
+    wsm = torch.empty(max(256, need.value), dtype=torch.uint8, device=J3.device)
+    emx = torch.empty_like(eri)
+
+    def timed(fn, k=5):
+        with torch.cuda.stream(stream):
+            fn()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(k):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    t64 = timed(lambda: P.ri_eri(B, 0, mb, 0, mb, out=eri, stream=stream))
+    tmx = timed(lambda: P.ri_eri_mixed(B, 0, mb, 0, mb, out=emx, ws=wsm, stream=stream))
+    dev = float((emx - eri).abs().max() / eri.abs().max())
+    info = int(info_box[0].item())  # 0: this (P|Q) factored (it is positive definite at FP64)
+    if not math.isfinite(dev):
+        dev = None  # a metric that did not factor leaves B undefined (and NaN is not JSON)
+    eflops = 2.0 * n * mb * mb
+    return {"ms": ms, "n_aux": n, "pairs": m, "eri_pairs": mb, "factor_info": info,
+            "fp64_flop": flops, "tflops": flops / (ms / 1e3) / 1e12,
+            "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal GB300 FP64",
+            "eri_block": {"fp64_ms": t64, "fp64_tflops": eflops / (t64 / 1e3) / 1e12, "tensor_ms": tmx,
+                          "tensor_useful_tflops": eflops / (tmx / 1e3) / 1e12, "tensor_max_dev_rel": dev}}
 
 
 def recorded_traffic(kernel, workload, precision):

@@ -80,6 +80,9 @@ SIGNATURES = [
     ("psq_ri_solve", _I, [_I, ctypes.c_int64, _VP, _VP, _VP]),
     ("psq_ri_eri", _I, [_I, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                         _VP, _VP]),
+    ("psq_ri_eri_mixed_workspace", _I, [_I, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_SZ)]),
+    ("psq_ri_eri_mixed", _I, [_I, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                              _VP, _VP, _SZ, _VP]),
 ]
 
 
@@ -148,6 +151,23 @@ def ri_eri(B, c0, nc, d0, nd, out=None, stream=None):
     m = B.numel() // n if n else 0
     out = torch.empty((nc, nd), dtype=torch.float64, device=B.device) if out is None else out
     _check(lib().psq_ri_eri(n, m, _dev_f64(B, "B"), c0, nc, d0, nd, _dev_f64(out, "out"), _stream_ptr(stream)))
+    return out
+
+
+def ri_eri_mixed(B, c0, nc, d0, nd, out=None, ws=None, stream=None):
+    """ri_eri on the tensor cores (8-bit slice products, ~2e-9 of the window-maximum bound);
+    ws: a uint8 CUDA tensor of at least ri_eri_mixed_workspace bytes (allocated if None).
+    Asynchronous."""
+    import torch
+    n = B.shape[0]
+    m = B.numel() // n if n else 0
+    need = ctypes.c_size_t()
+    _check(lib().psq_ri_eri_mixed_workspace(n, nc, nd, ctypes.byref(need)))
+    if ws is None:
+        ws = torch.empty(max(256, need.value), dtype=torch.uint8, device=B.device)
+    out = torch.empty((nc, nd), dtype=torch.float64, device=B.device) if out is None else out
+    _check(lib().psq_ri_eri_mixed(n, m, _dev_f64(B, "B"), c0, nc, d0, nd, _dev_f64(out, "out"),
+                                  ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
     return out
 
 

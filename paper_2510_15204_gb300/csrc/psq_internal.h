@@ -174,6 +174,10 @@ size_t ws_smem_bytes();
 cudaError_t prepare_kernels();  // per-device kernel attributes (context creation)
 cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
                         const float* ops, uint8_t* packed, cudaStream_t s);
+// Packed panels of the RI 4-index product from FP64 rows (panels[0] from srcA, panels[1] from
+// srcB, rows of n values); n_jobs covers both panels' packing jobs.
+cudaError_t launch_ri_pack(const Panel* panels, int64_t n_jobs, const double* srcA, const double* srcB, int n,
+                           uint8_t* packed, cudaStream_t s);
 // CTA b of the persistent contraction works through items [cta_begin[b], cta_begin[b + 1]).
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items,
                                const int* cta_begin, int n_ctas, const Panel* panels, const PairTile* ptiles,

@@ -616,6 +616,72 @@ __global__ void __launch_bounds__(512, 3) pack_kernel(const DevGrid* __restrict_
   pack_store(J, panels, packed);
 }
 
+// The same packed-panel image from FP64 operand rows (row-major, stride n): used for the
+// RI 4-index product, whose operand rows are the (P|ij) columns after the forward solve.
+// Panel k's rows start at src[k]; jobs as in pack_kernel, both panels' jobs in one launch.
+// The digits are taken in FP64 (exact: the value times a power of two, rounded digit by
+// digit), each exact in BF16.
+__global__ void __launch_bounds__(512, 2) ri_pack_kernel(const Panel* __restrict__ panels, const double* __restrict__ srcA,
+                                                      const double* __restrict__ srcB, int n, uint8_t* __restrict__ packed) {
+  using namespace mma;
+  const int64_t job = blockIdx.x;
+  const int k = panels[1].job_begin <= job ? 1 : 0;
+  const Panel& pn = panels[k];
+  const double* src = k ? srcB : srcA;
+  const int gsh = pn.tr >> 7;
+  const int lj = (int)(job - pn.job_begin);
+  const int tw = lj >> gsh, grp = lj & gsh;
+  const int t = tw / pn.nwin, w = tw - t * pn.nwin;
+  const int r = 64 * grp + (threadIdx.x >> 3), e8 = threadIdx.x & 7;
+  const int c = 2 * w + (e8 >> 2), qq = e8 & 3;
+  const int row = t * pn.tr + r;
+  const int k0 = 64 * c + 16 * qq;
+  double v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = 0.0;
+  if (row < pn.nrows && c < pn.nch) {
+    const double* rp = src + (int64_t)row * n + k0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (k0 + i < n) v[i] = rp[i];
+  }
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) mx = fmax(mx, fabs(v[i]));
+  const unsigned m8 = 0xffu << ((threadIdx.x & 31) & ~7u);
+  mx = fmax(mx, __shfl_xor_sync(m8, mx, 1));
+  mx = fmax(mx, __shfl_xor_sync(m8, mx, 2));
+  mx = fmax(mx, __shfl_xor_sync(m8, mx, 4));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);  // mx < 2^e <= 2 mx
+  if (!(mx > 0.0) || e < -110) e = kZeroExp;
+  if (e8 == 0) *reinterpret_cast<int*>(packed + pn.exp_off + (((int64_t)t * pn.nwin + w) * pn.tr + r) * 4) = e;
+  const int rt = min(pn.tr, pn.nrows - t * pn.tr);
+  if (c >= pn.nch || r >= rt) return;
+  const double sc = e == kZeroExp ? 0.0 : ldexp(1.0, 7 - e);
+  uint8_t* dst = packed + pn.pack_off + (int64_t)t * pn.nch * (4 * pn.tr * 128) + (int64_t)c * (4 * rt * 128);
+  const int plane = rt * 128;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    uint32_t o[kSlices][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double x0 = v[8 * j + 2 * q] * sc, x1 = v[8 * j + 2 * q + 1] * sc;
+#pragma unroll
+      for (int d = 0; d < kSlices; ++d) {
+        const double a0 = rint(x0), a1 = rint(x1);
+        const __nv_bfloat162 pr = __floats2bfloat162_rn((float)a0, (float)a1);
+        o[d][q] = *reinterpret_cast<const uint32_t*>(&pr);
+        x0 = (x0 - a0) * 256.0;
+        x1 = (x1 - a1) * 256.0;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < kSlices; ++d)
+      *reinterpret_cast<uint4*>(dst + d * plane + swz(r, 2 * qq + j)) = make_uint4(o[d][0], o[d][1], o[d][2], o[d][3]);
+  }
+}
+
 // ------------------------------------------------------------------ warp-specialised contraction
 //
 // One persistent CTA per SM, 512 threads, working through tiles (128 A rows x <= 64 B
@@ -1146,6 +1212,13 @@ cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, con
   if (n_ctas == 0) return cudaSuccess;
   contract_ws_kernel<<<n_ctas, ws::kThreads, ws_smem_bytes(), s>>>(grids, blocks, items, cta_begin, panels, ptiles, ops,
                                                                    packed, part, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ri_pack(const Panel* panels, int64_t n_jobs, const double* srcA, const double* srcB, int n,
+                           uint8_t* packed, cudaStream_t s) {
+  if (n_jobs == 0) return cudaSuccess;
+  ri_pack_kernel<<<(unsigned)n_jobs, 512, 0, s>>>(panels, srcA, srcB, n, packed);
   return cudaGetLastError();
 }
 

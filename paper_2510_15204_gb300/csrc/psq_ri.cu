@@ -6,6 +6,7 @@
 // every loop bound is a size argument (no waits).
 #include "psq_internal.h"
 
+#include <algorithm>
 #include <cstdint>
 
 namespace psq {
@@ -216,6 +217,119 @@ __global__ void __launch_bounds__(256) eri_kernel(int n, int64_t m, const double
   }
 }
 
+// ---------------------------------------------------------------- tensor-core product
+//
+// (ij|kl) = sum_R B[R][ij] B[R][kl] is the contraction of eq 9 with the aux index R in the
+// place of the points: the pair columns of B become operand rows (transposed into Bt), are
+// packed as in the mixed path (four 8-bit slices per value under a power-of-two scale per
+// row and 128 aux functions), and the tcgen05 contraction and its FP64 range reduction run
+// unchanged on them (one block, A = the c pairs, B = the d pairs, all row constants 1).
+
+constexpr size_t kAlign = 256;
+size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct RiMixedLayout {
+  int64_t nc, nd;
+  int n, nch, nwin, tmA, tnB, n_ranges, win_per, n_ctas;
+  int64_t n_items, jobsA, jobsB;
+  size_t o_grid, o_pn, o_blk, o_items, o_cb, o_rows, o_rowc, o_eb, o_status, o_bt, o_pack, o_part, total;
+  int64_t packA, expA, packB, expB;  // panel offsets within the packed area
+};
+
+RiMixedLayout ri_mixed_layout(int n, int64_t nc, int64_t nd, int sm_count) {
+  RiMixedLayout L{};
+  L.n = n; L.nc = nc; L.nd = nd;
+  L.nch = (n + 63) / 64;
+  L.nwin = (L.nch + 1) / 2;
+  L.tmA = (int)((nc + 127) / 128);
+  L.tnB = (int)((nd + 63) / 64);
+  const int64_t tiles = (int64_t)L.tmA * L.tnB;
+  const int64_t want = 2LL * sm_count;  // at least two items per SM: ranges of aux windows
+  int r = tiles >= want ? 1 : (int)std::min<int64_t>(L.nwin, (want + tiles - 1) / tiles);
+  L.win_per = (L.nwin + r - 1) / r;
+  L.n_ranges = (L.nwin + L.win_per - 1) / L.win_per;
+  L.n_items = tiles * L.n_ranges;
+  L.n_ctas = (int)std::min<int64_t>(L.n_items, sm_count);
+  L.jobsA = (int64_t)L.tmA * L.nwin * 2;
+  L.jobsB = (int64_t)L.tnB * L.nwin;
+  size_t o = 0;
+  auto sec = [&](size_t bytes) { const size_t at = o; o = up(o + bytes); return at; };
+  L.o_status = sec(sizeof(int));
+  L.o_grid = sec(sizeof(DevGrid));
+  L.o_pn = sec(2 * sizeof(Panel));
+  L.o_blk = sec(sizeof(MmaBlock));
+  L.o_items = sec(sizeof(GemmItem) * (size_t)L.n_items);
+  L.o_cb = sec(sizeof(int) * (size_t)(L.n_ctas + 1));
+  L.o_rows = sec(sizeof(short2) * (size_t)(nc + nd));
+  L.o_rowc = sec(sizeof(double));
+  L.o_eb = sec(2 * sizeof(int64_t));
+  L.o_bt = sec(sizeof(double) * (size_t)(nc + nd) * n);
+  size_t pk = 0;
+  auto psec = [&](size_t bytes) { const size_t at = pk; pk = up(pk + bytes); return (int64_t)at; };
+  L.packA = psec((size_t)nc * L.nch * 4 * 128);
+  L.expA = psec((size_t)L.tmA * L.nwin * 128 * 4);
+  L.packB = psec((size_t)nd * L.nch * 4 * 128);
+  L.expB = psec((size_t)L.tnB * L.nwin * 64 * 4);
+  L.o_pack = sec(pk);
+  L.o_part = sec(sizeof(float2) * (size_t)L.n_ranges * nc * nd);
+  L.total = o;
+  return L;
+}
+
+// The tables of the one-block plan, written on the device (nothing to stage on the host, so
+// the call can be captured in a CUDA graph).  Items dealt round-robin, stored per CTA.
+__global__ void ri_setup_kernel(RiMixedLayout L, char* __restrict__ ws) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    *reinterpret_cast<int*>(ws + L.o_status) = 0;
+    DevGrid* g = reinterpret_cast<DevGrid*>(ws + L.o_grid);
+    g->K = L.n;
+    g->rc_off = 0;
+    Panel* pn = reinterpret_cast<Panel*>(ws + L.o_pn);
+    pn[0].grid = 0; pn[0].rows_off = 0; pn[0].nrows = (int)L.nc; pn[0].tr = 128; pn[0].n_tiles = L.tmA;
+    pn[0].nch = L.nch; pn[0].nwin = L.nwin; pn[0].pack_off = L.packA; pn[0].exp_off = L.expA; pn[0].job_begin = 0;
+    pn[1].grid = 0; pn[1].rows_off = (int)L.nc; pn[1].nrows = (int)L.nd; pn[1].tr = 64; pn[1].n_tiles = L.tnB;
+    pn[1].nch = L.nch; pn[1].nwin = L.nwin; pn[1].pack_off = L.packB; pn[1].exp_off = L.expB; pn[1].job_begin = L.jobsA;
+    MmaBlock* b = reinterpret_cast<MmaBlock*>(ws + L.o_blk);
+    b->grid = 0; b->m = (int)L.nc; b->n = (int)L.nd; b->a_off = 0; b->b_off = (int)L.nc;
+    b->n_ranges = L.n_ranges; b->win_per = L.win_per; b->a_panel = 0; b->b_panel = 1;
+    b->ptile_off = 0; b->n_btiles = 0; b->res_off = 0; b->part_off = 0;
+    *reinterpret_cast<double*>(ws + L.o_rowc) = 1.0;
+    int64_t* eb = reinterpret_cast<int64_t*>(ws + L.o_eb);
+    eb[0] = 0;
+    eb[1] = L.nc * L.nd;
+  }
+  const int64_t q = L.n_items / L.n_ctas, rem = L.n_items % L.n_ctas;
+  if (i <= L.n_ctas) reinterpret_cast<int*>(ws + L.o_cb)[i] = (int)(i * q + (i < rem ? i : rem));
+  if (i < L.n_items) {
+    const int64_t tiles = (int64_t)L.tmA * L.tnB;
+    const int chunk = (int)(i / tiles), t = (int)(i % tiles);
+    const int64_t bcta = i % L.n_ctas, j = i / L.n_ctas;
+    const int64_t slot = bcta * q + (bcta < rem ? bcta : rem) + j;
+    reinterpret_cast<GemmItem*>(ws + L.o_items)[slot] = GemmItem{0, t / L.tnB, t % L.tnB, chunk};
+  }
+  if (i < L.nc + L.nd) reinterpret_cast<short2*>(ws + L.o_rows)[i] = make_short2(0, -1);
+}
+
+// Bt[r][R] = B[R][col0 + r] for r < count: the pair columns as rows (32 x 32 tiles).
+__global__ void ri_transpose_kernel(int n, int64_t m, const double* __restrict__ B, int64_t col0, int64_t count,
+                                    double* __restrict__ Bt) {
+  __shared__ double tile[32][33];
+  const int64_t c0 = (int64_t)blockIdx.x * 32;
+  const int R0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int R = R0 + k;
+    const int64_t c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = (R < n && c < count) ? B[(int64_t)R * m + col0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k;
+    const int R = R0 + threadIdx.x;
+    if (c < count && R < n) Bt[c * n + R] = tile[threadIdx.x][k];
+  }
+}
+
 bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 psq_status launched() {
@@ -280,5 +394,59 @@ extern "C" psq_status psq_ri_eri(int n, int64_t m, const double* d_B, int64_t c0
   if ((nc + 63) / 64 > 65535 || (nd + 63) / 64 > 0x7fffffff) return set_error(PSQ_ERR_ARG, "psq_ri_eri: block too large");
   eri_kernel<<<dim3((unsigned)((nd + 63) / 64), (unsigned)((nc + 63) / 64)), 256, 0, (cudaStream_t)stream>>>(
       n, m, d_B, c0, nc, d0, nd, d_out);
+  return launched();
+}
+
+extern "C" psq_status psq_ri_eri_mixed_workspace(int n, int64_t nc, int64_t nd, size_t* bytes) {
+  if (!bytes) return set_error(PSQ_ERR_ARG, "psq_ri_eri_mixed_workspace: bytes is NULL");
+  if (n < 0 || nc < 0 || nd < 0) return set_error(PSQ_ERR_ARG, "psq_ri_eri_mixed_workspace: negative size");
+  if (nc > (1 << 30) || nd > (1 << 30)) return set_error(PSQ_ERR_UNSUPPORTED, "psq_ri_eri_mixed_workspace: block too large");
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *bytes = ri_mixed_layout(n, nc, nd, sms).total;
+  return PSQ_OK;
+}
+
+extern "C" psq_status psq_ri_eri_mixed(int n, int64_t m, const double* d_B, int64_t c0, int64_t nc, int64_t d0,
+                                       int64_t nd, double* d_out, void* d_workspace, size_t ws_bytes, void* stream) {
+  if (n < 0 || m < 0 || nc < 0 || nd < 0) return set_error(PSQ_ERR_ARG, "psq_ri_eri_mixed: negative size");
+  if (c0 < 0 || d0 < 0 || c0 + nc > m || d0 + nd > m)
+    return set_error(PSQ_ERR_ARG, "psq_ri_eri_mixed: range outside [0, m)");
+  if (nc == 0 || nd == 0) return PSQ_OK;
+  if (!d_out || !aligned8(d_out) || (n > 0 && (!d_B || !aligned8(d_B))))
+    return set_error(PSQ_ERR_ARG, "psq_ri_eri_mixed: NULL or misaligned pointer");
+  if (!d_workspace || (uintptr_t)d_workspace % kAlign)
+    return set_error(PSQ_ERR_ARG, "psq_ri_eri_mixed: workspace NULL or not 256-byte aligned");
+  if (nc > (1 << 30) || nd > (1 << 30)) return set_error(PSQ_ERR_UNSUPPORTED, "psq_ri_eri_mixed: block too large");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n == 0) {
+    if (cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)nc * nd, s) != cudaSuccess) return launched();
+    return PSQ_OK;
+  }
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return launched();
+  const RiMixedLayout L = ri_mixed_layout(n, nc, nd, sms);
+  if (ws_bytes < L.total) return set_error(PSQ_ERR_OOM, "psq_ri_eri_mixed: workspace too small");
+  if (prepare_kernels() != cudaSuccess) return launched();
+  char* ws = (char*)d_workspace;
+  if (cudaMemsetAsync(ws, 0, L.o_bt, s) != cudaSuccess) return launched();  // tables (zeroed, then set)
+  const int64_t setup_n = std::max<int64_t>(std::max<int64_t>(L.n_items, nc + nd), L.n_ctas + 1);
+  ri_setup_kernel<<<(unsigned)((setup_n + 255) / 256), 256, 0, s>>>(L, ws);
+  double* btA = (double*)(ws + L.o_bt);
+  double* btB = btA + (size_t)nc * n;
+  ri_transpose_kernel<<<dim3((unsigned)((nc + 31) / 32), (n + 31) / 32), dim3(32, 8), 0, s>>>(n, m, d_B, c0, nc, btA);
+  ri_transpose_kernel<<<dim3((unsigned)((nd + 31) / 32), (n + 31) / 32), dim3(32, 8), 0, s>>>(n, m, d_B, d0, nd, btB);
+  uint8_t* packed = (uint8_t*)(ws + L.o_pack);
+  const Panel* pn = (const Panel*)(ws + L.o_pn);
+  if (launch_ri_pack(pn, L.jobsA + L.jobsB, btA, btB, n, packed, s) != cudaSuccess) return launched();
+  if (launch_contract_ws((const DevGrid*)(ws + L.o_grid), (const MmaBlock*)(ws + L.o_blk),
+                         (const GemmItem*)(ws + L.o_items), (const int*)(ws + L.o_cb), L.n_ctas, pn, nullptr, nullptr,
+                         packed, (float2*)(ws + L.o_part), (int*)(ws + L.o_status), s) != cudaSuccess)
+    return launched();
+  if (launch_reduce_mixed((const DevGrid*)(ws + L.o_grid), (const MmaBlock*)(ws + L.o_blk), 1,
+                          (const int64_t*)(ws + L.o_eb), nc * nd, (const short2*)(ws + L.o_rows),
+                          (const double*)(ws + L.o_rowc), (const float2*)(ws + L.o_part), d_out, s) != cudaSuccess)
+    return launched();
   return launched();
 }

@@ -154,3 +154,51 @@ def test_triatomic_eri_parity(P):
     nb = job.n_bf
     e4 = eri.reshape(nb, nb, nb, nb)
     assert np.abs(e4 - e4.transpose(2, 3, 0, 1)).max() <= 50 * kappa * EPS * np.abs(eri).max()
+
+
+def window_bound(Ba, Bb):
+    """sum over 128-row aux windows of (rows in the window) x (window max |a|) x (window max |b|)
+    per element: the scale the slices resolve to 2^-31 (each value keeps 31 bits relative to
+    its window's largest)."""
+    out = 0.0
+    for w0 in range(0, Ba.shape[0], 128):
+        ma = np.abs(Ba[w0:w0 + 128]).max(axis=0)
+        mb = np.abs(Bb[w0:w0 + 128]).max(axis=0)
+        out = out + min(128, Ba.shape[0] - w0) * np.outer(ma, mb)
+    return out
+
+
+@pytest.mark.parametrize("n,m,blk", [(1, 9, (0, 9, 0, 9)), (37, 150, (17, 70, 90, 60)), (82, 676, (0, 676, 0, 676)),
+                                     (200, 3000, (100, 1300, 500, 700))])
+def test_eri_mixed_within_stated_error(P, n, m, blk):
+    """Tensor-core (ij|kl) against the FP64 product: within 2e-9 (about 4 x 2^-31) of the
+    window bound; ragged aux counts, pair ranges and blocks, aux rows of scales e^-3..e^3."""
+    import torch
+    rng = np.random.default_rng(n + m)
+    B = rng.standard_normal((n, m)) * np.exp(rng.uniform(-3, 3, (n, 1)))
+    c0, nc, d0, nd = blk
+    ref = B[:, c0:c0 + nc].T @ B[:, d0:d0 + nd]
+    got = P.ri_eri_mixed(torch.tensor(B, device="cuda"), c0, nc, d0, nd)
+    torch.cuda.synchronize()
+    err = np.abs(got.cpu().numpy() - ref) / window_bound(B[:, c0:c0 + nc], B[:, d0:d0 + nd])
+    assert err.max() < 2e-9, err.max()
+
+
+def test_eri_mixed_on_the_triatomic_assembly(P):
+    """The RI product of the triatomic job's FP64 (P|Q), (P|ij) on the tensor cores against the
+    FP64 kernel: within 2e-9 of the window bound."""
+    import torch
+    job = synth.triatomic_oh2(0)
+    J = P.Job.from_synth(P.Context(0), job, P.FP64)
+    out = J.compute(oracle.J2 | oracle.J3)
+    n = out["J2"].shape[0]
+    L, info = P.ri_factor(out["J2"])
+    B = P.ri_solve(L, out["J3"].reshape(n, -1).clone())
+    m = B.shape[1]
+    e64 = P.ri_eri(B, 0, m, 0, m)
+    emx = P.ri_eri_mixed(B, 0, m, 0, m)
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    Bh = B.cpu().numpy()
+    err = np.abs(emx.cpu().numpy() - e64.cpu().numpy()) / window_bound(Bh, Bh)
+    assert err.max() < 2e-9, err.max()
