@@ -181,3 +181,10 @@ def test_ri_entry_points_validate_arguments_without_a_gpu(P):
     assert L.psq_ri_eri(3, 10, dummy, 8, 5, 0, 2, dummy, None) == 1  # c0 + nc > m
     assert L.psq_ri_eri(3, 10, dummy, 0, 2, -1, 2, dummy, None) == 1
     assert L.psq_ri_eri(3, 10, dummy, 0, 0, 0, 4, None, None) == 0  # empty block
+    nbytes = ctypes.c_size_t()
+    assert L.psq_ri_eri_mixed_workspace(-1, 4, 4, ctypes.byref(nbytes)) == 1
+    assert L.psq_ri_eri_mixed_workspace(82, 676, 676, None) == 1
+    assert L.psq_ri_eri_mixed_workspace(82, 676, 676, ctypes.byref(nbytes)) == 0 and nbytes.value > 676 * 676 * 8
+    assert L.psq_ri_eri_mixed(3, 10, dummy, 8, 5, 0, 2, dummy, dummy, 1 << 20, None) == 1  # c0 + nc > m
+    assert L.psq_ri_eri_mixed(3, 10, dummy, 0, 2, 0, 2, dummy, ctypes.c_void_p(64 + 8), 1 << 20, None) == 1  # ws align
+    assert L.psq_ri_eri_mixed(3, 10, dummy, 0, 0, 0, 2, None, None, 0, None) == 0  # empty block
