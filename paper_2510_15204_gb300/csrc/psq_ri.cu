@@ -1,9 +1,10 @@
 // RI 4-index assembly (Section 3, eq 14): (ij|kl) ~ sum_PQ (ij|P) [(PQ)^-1] (Q|kl).  The metric
 // (P|Q) is factored as L L^T (blocked right-looking Cholesky), B = L^-1 (P|ij) by blocked
-// forward substitution, and (ij|kl) = sum_R B[R][ij] B[R][kl] by a tiled FP64 product.  All
-// FP64 on the CUDA cores: the metric is ill-conditioned enough that the factor and the solve
-// need it, and these steps are small next to the integrals themselves.  Blocks of 32 rows;
-// every loop bound is a size argument (no waits).
+// forward substitution, and (ij|kl) = sum_R B[R][ij] B[R][kl] by a tiled FP64 product or,
+// for large blocks, on the tensor cores through the mixed path's packing and contraction.
+// The factor and the solve stay FP64 on the CUDA cores: the metric is ill-conditioned enough
+// to need it.  Blocks of 32 rows; every loop bound is a size argument (no waits outside the
+// contraction's own bounded ones).
 #include "psq_internal.h"
 
 #include <algorithm>
