@@ -53,7 +53,7 @@ def test_c3h6_sampled_blocks(ref, precision, tol):
     ax = _fn_slices(job.aux, job.n_atoms)
     worst = {}
 
-    floor = 0.0 if precision == 0 else 1e-4  # mixed: errors are judged against 1e-4 of the class scale
+    floor = 0.0 if precision == 0 else 1e-4  # mixed: errors are measured against 1e-4 of the class scale
 
     def check(k, idx):
         scale = np.maximum(np.abs(R[k][idx]), R["abs" + k][idx])
