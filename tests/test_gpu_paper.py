@@ -106,3 +106,14 @@ def test_of2_third_centre_split_fig_5(P, ctx):
          for nsp in (1, 2, 3, 4)]
     assert e[1] < 0.6 * e[0], e
     assert max(e[2], e[3]) < 2.0 * e[1], e
+
+
+def test_so2_tz_smallest_overlap_eigenvalue_on_the_gpu(P, ctx):
+    """The one value this path's paper prints for a whole matrix: the smallest eigenvalue of
+    SO2's TZ overlap matrix, 1.3e-5 (Section 4), on the PS grid 26/32/14, Q 4 (Table 1's
+    BP-sized grid), through the FP64 CUDA path (and the mixed path to its error)."""
+    job = synth.paper_job("SO2", spec=(26, 32, 14, 4, 4, 4, 3), mask=oracle.S)
+    for prec in (P.FP64, P.MIXED):
+        S = run(P, ctx, job, oracle.S, prec)["S"]
+        ev = np.linalg.eigvalsh(0.5 * (S + S.T))[0]
+        assert float("%.1e" % ev) == 1.3e-5, (prec, ev)
