@@ -62,10 +62,11 @@ typedef struct { int n_mu, n_nu, n_phi, q_mu, q_nu, q_phi, n_sp; } psq_grid_spec
 typedef enum {
   PSQ_FP64 = 0,  /* plain path: every step in FP64 */
   PSQ_MIXED = 1  /* FP64 node tables, third-centre offsets, row constants and range sums;
-                    FP32 weights, STO values and aux potentials; contraction on tcgen05
-                    tensor cores: four 8-bit integer slices per value in BF16 under a
-                    power-of-two scale per row and 128-point window, the slice products of
-                    orders 0..3 accumulated exactly in FP32 */
+                    double-float (FP32 hi + lo, ~48 bits) weights, STO values and aux
+                    potentials; contraction on tcgen05 tensor cores: five 8-bit integer slices
+                    per value in BF16 under a power-of-two scale per row and 128-point window
+                    (39 bits of the window's largest value), the slice products of orders
+                    0..4 accumulated exactly in FP32 and folded into double-float sums */
 } psq_precision;
 
 enum { PSQ_S = 1, PSQ_T = 2, PSQ_V = 4, PSQ_J2 = 8, PSQ_J3 = 16, PSQ_ALL = 31 };
@@ -95,6 +96,15 @@ psq_status psq_job_sizes(const psq_job* job, int* n_bf, int* n_aux);
 /* Device workspace bytes psq_compute needs for the classes in mask. */
 psq_status psq_job_workspace(const psq_job* job, unsigned mask, size_t* bytes);
 
+/* Workspace bound of the PSQ_MIXED path (no paper counterpart).  Its grids are processed in
+ * waves of consecutive grids whose double-float operand rows and packed panels together stay
+ * within `bytes` (a wave holds at least one grid; 0 selects the default, 6 GiB); the operand,
+ * packed and partial-sum regions of the workspace are shared by the waves, so the workspace is
+ * about the largest wave plus the result blocks.  Plans (and captured graphs) made before are
+ * dropped; later calls plan with the new bound.  No effect on PSQ_FP64 jobs.  Errors:
+ * PSQ_ERR_ARG for a NULL job. */
+psq_status psq_job_set_wave_budget(psq_job* job, size_t bytes);
+
 /* Job statistics: number of grids, total quadrature points (over the grids mask needs),
  * useful contractions (sum over integrated blocks of rows x cols x points, each (P,i<=j)
  * once on a same-atom pair), and kernel launches psq_compute issues for mask. */
@@ -115,8 +125,8 @@ psq_status psq_job_autotune(psq_job* job, unsigned mask, void* d_workspace, size
 
 /* Floating-point operations the contraction kernel issues in one psq_compute for mask (the
  * measure a tensor-pipe roofline counts; no paper counterpart).  PSQ_MIXED: every tensor-core
- * MMA of the 8-bit slice products, tiles of 128 rows x 64 columns whatever their fill, 10
- * slice products per 64-point chunk, each M x N x K MMA counting 2MNK.  PSQ_FP64: 2 x rows x cols x
+ * MMA of the 8-bit slice products, tiles of 128 rows x 48 columns whatever their fill, 15
+ * slice products per 32-point chunk, each M x N x K MMA counting 2MNK.  PSQ_FP64: 2 x rows x cols x
  * points summed over the computed blocks.  Errors: PSQ_ERR_ARG for NULL pointers or unknown
  * mask bits. */
 psq_status psq_job_issued_flops(const psq_job* job, unsigned mask, double* flops);
@@ -169,8 +179,18 @@ psq_status psq_profile_read(psq_job* job, double ms[8], int counts[8]);
 psq_status psq_compute_noalloc(psq_job* job, unsigned mask, double* d_out[5], void* stream);
 
 /* Waits for `stream` and reports whether a kernel of the last psq_compute on this workspace
- * gave up a bounded wait (PSQ_ERR_TIMEOUT); psq_compute_host calls it itself. */
+ * gave up a bounded wait (PSQ_ERR_TIMEOUT); psq_compute_host calls it itself.  d_workspace
+ * NULL reads the status of the last psq_compute_noalloc on the current device. */
 psq_status psq_check(psq_job* job, unsigned mask, void* d_workspace, void* stream);
+
+/* Failure detection (no paper counterpart): the limit, in nanoseconds, of every bounded wait
+ * in the main loops of the tensor-core contraction for this job's later psq_compute calls
+ * (default 4e9; 1 <= ns <= 6e10).  A wait that runs out makes the kernel record a status
+ * (psq_check then returns PSQ_ERR_TIMEOUT), stop its loops, wait (4 s at most) for its own
+ * copies and MMAs in flight, release its tensor memory and return: the context stays usable
+ * and the next psq_compute starts afresh.  Graphs captured before keep the limit they were
+ * captured with.  Errors: PSQ_ERR_ARG for a NULL job or a limit out of range. */
+psq_status psq_job_set_wait_limit(psq_job* job, uint64_t ns);
 
 /* Diagnostics for step-by-step parity tests. */
 /* Grid g of the PSQ_ALL plan (0 <= g < n_grids; pair grids (A<B) first, then the refined
@@ -186,7 +206,9 @@ psq_status psq_job_grid_points(psq_job* job, int g, void* d_workspace, size_t ws
 /* Evaluates on grid g: kind 0 = basis chi of the grid's two pair atoms (rows in function
  * order), 1 = their kinetic operand lap chi, 2 = aux chi, 3 = aux potentials V^P (aux of
  * both pair atoms for an unrefined grid, of the third centre for a refined one).  d_out
- * holds rows x n_points doubles; *rows receives the row count. */
+ * holds rows x n_points doubles; *rows receives the row count.  A PSQ_FP64 job evaluates in
+ * FP64; a PSQ_MIXED job runs the mixed path's evaluation (double-float values of x = zeta r
+ * and the direction) and returns them times their FP64 row constants. */
 psq_status psq_job_grid_functions(psq_job* job, int g, int kind, void* d_workspace,
                                   size_t ws_bytes, double* d_out, int* rows, void* stream);
 

@@ -69,6 +69,8 @@ SIGNATURES = [
     ("psq_profile_enable", _I, [_VP, _I]),
     ("psq_profile_read", _I, [_VP, _PD, ctypes.POINTER(_I)]),
     ("psq_check", _I, [_VP, _U, _VP, _VP]),
+    ("psq_job_set_wait_limit", _I, [_VP, ctypes.c_uint64]),
+    ("psq_job_set_wave_budget", _I, [_VP, _SZ]),
     ("psq_compute_noalloc", _I, [_VP, _U, ctypes.POINTER(_VP), _VP]),
     ("psq_server_create", _I, [_VP, _VP, _SZ, _I, ctypes.POINTER(_VP)]),
     ("psq_server_submit", _I, [_VP, _VP, _U, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_uint64)]),
@@ -320,8 +322,18 @@ class Job:
         return host_out
 
     def check(self, mask, ws, stream=None):
-        """Waits for the stream; raises PsqError(PSQ_ERR_TIMEOUT) if a kernel gave up a wait."""
-        _check(lib().psq_check(self.handle, mask, ctypes.c_void_p(ws.data_ptr()), _stream_ptr(stream)))
+        """Waits for the stream; raises PsqError(PSQ_ERR_TIMEOUT) if a kernel gave up a wait.
+        ws None: the allocation-free entry point's scratch on the current device."""
+        ptr = None if ws is None else ctypes.c_void_p(ws.data_ptr())
+        _check(lib().psq_check(self.handle, mask, ptr, _stream_ptr(stream)))
+
+    def set_wave_budget(self, nbytes: int):
+        """psq_job_set_wave_budget: the mixed path's operand + packed bytes per wave (0: default)."""
+        _check(lib().psq_job_set_wave_budget(self.handle, int(nbytes)))
+
+    def set_wait_limit(self, ns: int):
+        """psq_job_set_wait_limit: the bound of the contraction's device waits, nanoseconds."""
+        _check(lib().psq_job_set_wait_limit(self.handle, int(ns)))
 
     def io_bytes(self, mask=ALL):
         h, d = ctypes.c_size_t(), ctypes.c_size_t()

@@ -57,6 +57,7 @@ constexpr double kOnAxisTol = 1e-10;  // a third centre this close (x a) to the 
 constexpr int kPointsPerBlock = 128;
 constexpr int64_t kMaxChunkPoints = 32768;  // FP64 path: points per sequential partial sum
 constexpr int kSmCount = 152;
+constexpr size_t kDefaultWaveBytes = (size_t)6 << 30;  // mixed path: operand + packed bytes per wave
 
 // Gauss-Legendre rule by Newton's method on P_q (Bonnet recurrence); nodes ascending.
 void gauss_legendre(int q, double* x, double* w) {
@@ -139,14 +140,24 @@ struct Plan {
   std::vector<Panel> panels;
   std::vector<PairTile> ptiles;
   int64_t n_pack_jobs = 0, pack_bytes = 0;
-  std::vector<int> cta_begin;  // contraction: CTA b takes items [cta_begin[b], cta_begin[b + 1])
+  std::vector<int> cta_begin;  // contraction: CTA b of wave k takes items [cta_begin[cb_off + b], .. + 1])
   int n_ctas = 0;
+  // Waves (mixed path): consecutive grids whose operand rows and packed panels fit the wave
+  // budget together; each wave runs evaluation, packing, contraction and range reduction in
+  // the shared operand / packed / partial regions (offsets of its grids, panels and blocks
+  // are relative to them), the blocks' results stay in the one result region.
+  struct Wave {
+    int g0, g1, pb0, pb1, pn0, pn1, mb0, mb1, cb_off, n_ctas;
+    int64_t jobs;
+  };
+  std::vector<Wave> waves;
   size_t o_cb = 0;
   size_t o_mb = 0, o_mi = 0, o_pn = 0, o_pt = 0, nodes_off = 0, o_xi = 0, o_rc = 0, pack_off = 0;
   std::vector<float2> xi;    // per grid: (hi, lo) scale turning rho into x = zeta r, per shell
   std::vector<double> rowc;  // per grid: FP64 constant of every operand row
   int64_t n_nodes = 0;
   int max_node_entries = 0;
+  int64_t n_ops = 0;  // operand elements (mixed path: the lo plane follows the hi plane)
   double* staging = nullptr;  // copy of the tables, page-locked when pinned
   bool pinned = false;
   int64_t n_points = 0;
@@ -172,8 +183,10 @@ struct psq_job {
   std::vector<int> nb, na, sb0, sb1, sa0, sa1, fn_atom, fn_local, aux_atom, aux_local, nn;
   std::vector<DevShell> dbs, das;
   int nbf = 0, naux = 0;
-  std::map<unsigned, std::unique_ptr<Plan>> plans;
+  std::map<unsigned, std::shared_ptr<Plan>> plans;  // shared: a running compute keeps its plan alive
   std::map<unsigned, int> work_split;  // per mask, chosen by psq_job_autotune
+  uint64_t wait_ns = 4000000000ull;    // limit of every bounded device wait (psq_job_set_wait_limit)
+  size_t wave_bytes = 0;               // mixed path: operand + packed bytes per wave (0: default)
   std::mutex mu;
   // launch timing: events recorded on the compute stream, read back on request
   struct ProfRec { int kind; cudaEvent_t ev; };
@@ -341,6 +354,41 @@ psq_status build_grid(const psq_job* j, GridKey key, DevGrid& g, std::vector<dou
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+double klm_norm(int l, int m) {
+  const int am = std::abs(m);
+  const double k = std::sqrt((2 * l + 1) / (4 * M_PI) * factorial(l - am) / factorial(l + am));
+  return m != 0 ? k * std::sqrt(2.0) : k;
+}
+
+// FP64 constants of the mixed path's operand rows of one kind on grid g (kind 0 basis chi,
+// 1 lap chi, 2 aux chi, 3 aux V^P; rows in function order of the grid's centres): the FP32/df
+// row values are functions of x = zeta r and of the direction only, times
+//   chi: N K_lm zeta^-(n-1);  lap chi: N K_lm zeta^-(n-1) zeta^2;
+//   V^P: 4 pi/(2l+1) N K_lm zeta^-(n+1)  (eq 16 through the Laplace expansion).
+void row_constants(const psq_job* j, const DevGrid& g, int kind, std::vector<double>& out) {
+  if (kind <= 1) {
+    for (int c = 0; c < 2; ++c) {
+      const int s0 = c == 0 ? g.shb_A0 : g.shb_B0, s1 = c == 0 ? g.shb_A1 : g.shb_B1;
+      for (int q = s0; q < s1; ++q) {
+        const DevShell& d = j->dbs[q];
+        for (int m = -d.l; m <= d.l; ++m)
+          out.push_back(d.norm * klm_norm(d.l, m) * std::pow(d.zeta, -(d.n - 1) + (kind == 1 ? 2.0 : 0.0)));
+      }
+    }
+    return;
+  }
+  for (int c = 0; c < 2; ++c) {
+    const int s0 = c == 0 ? g.sha_0 : g.sha_2, s1 = c == 0 ? g.sha_1 : g.sha_3;
+    if ((c == 0 ? g.aux_c0 : g.aux_c1) < 0) continue;
+    for (int q = s0; q < s1; ++q) {
+      const DevShell& d = j->das[q];
+      for (int m = -d.l; m <= d.l; ++m)
+        out.push_back(kind == 3 ? 4.0 * M_PI / (2 * d.l + 1) * d.norm * klm_norm(d.l, m) * std::pow(d.zeta, -(d.n + 1))
+                                : d.norm * klm_norm(d.l, m) * std::pow(d.zeta, -(d.n - 1)));
+    }
+  }
+}
 
 psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   P.mask = mask;
@@ -544,14 +592,14 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       Panel pn{};
       pn.grid = g; pn.rows_off = rows_off; pn.nrows = nrows; pn.tr = tr;
       pn.n_tiles = (nrows + tr - 1) / tr;
-      pn.nch = (int)((G.K + 63) / 64);
-      pn.nwin = (pn.nch + 1) / 2;
+      pn.nch = (int)((G.K + kChunkPts - 1) / kChunkPts);
+      pn.nwin = (int)((G.K + kWinPts - 1) / kWinPts);
       pn.pack_off = P.pack_bytes;
-      P.pack_bytes += (int64_t)align_up((size_t)nrows * pn.nch * 4 * 128, 256);
+      P.pack_bytes += (int64_t)align_up((size_t)nrows * pn.nch * kSlices * 2 * kChunkPts, 256);
       pn.exp_off = P.pack_bytes;
       P.pack_bytes += (int64_t)align_up((size_t)pn.n_tiles * pn.nwin * tr * 4, 256);
       pn.job_begin = P.n_pack_jobs;
-      P.n_pack_jobs += (int64_t)pn.n_tiles * pn.nwin * (tr / 64);  // 64-row groups
+      P.n_pack_jobs += (int64_t)pn.n_tiles * pn.nwin * (tr / kPackRows);  // 16-row groups
       P.panels.push_back(pn);
       return (int)P.panels.size() - 1;
     };
@@ -582,7 +630,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       };
       for (const PairRef& pr : pl) {
         const int need = (slot(pr.x) < 0) + (pr.y != pr.x && slot(pr.y) < 0);
-        if (t.ncols == 64 || t.nrows + need > kPairTileRows) flush();
+        if (t.ncols == kMmaN || t.nrows + need > kPairTileRows) flush();
         int sx = slot(pr.x);
         if (sx < 0) { sx = t.nrows; t.rows[t.nrows++] = (short)pr.x; }
         int sy = slot(pr.y);
@@ -606,7 +654,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
         if (j3 || j2) {
           u_off = (int)P.pairs.size();
           for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
-          pu = add_panel((int)gi, u_off, g.nG, 128);
+          pu = add_panel((int)gi, u_off, g.nG, kMmaM);
         }
         if (j3) {
           // all local pairs i <= j, result columns in packed row-major order
@@ -614,9 +662,10 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
           for (int i = 0; i < nl; ++i)
             for (int jj = i; jj < nl; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + jj));
           std::vector<PairRef> pl;
-          for (int ib = 0; ib < nl; ib += 8)
-            for (int jb = ib; jb < nl; jb += 8)
-              for (int i = ib; i < std::min(nl, ib + 8); ++i)
+          // 6 x 8 blocks of (i, j): 48 columns from at most 14 distinct rows
+          for (int ib = 0; ib < nl; ib += 6)
+            for (int jb = ib / 8 * 8; jb < nl; jb += 8)
+              for (int i = ib; i < std::min(nl, ib + 6); ++i)
                 for (int jj = std::max(i, jb); jj < std::min(nl, jb + 8); ++jj)
                   pl.push_back(PairRef{i * nl - i * (i - 1) / 2 + (jj - i), g.row_F + i, g.row_F + jj});
           const auto tl = add_pair_tiles(pl);
@@ -640,16 +689,16 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
             for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_F + i, W + 2));
           }
           const int na_rows = (int)P.pairs.size() - a_off;
-          const int pk = add_panel((int)gi, a_off, na_rows, 128);
+          const int pk = add_panel((int)gi, a_off, na_rows, kMmaM);
           const int b_off = (int)P.pairs.size();
           for (int i = 0; i < nl; ++i) P.pairs.push_back(make_short2(g.row_F + i, -1));
-          const int pf = add_panel((int)gi, b_off, nl, 64);
+          const int pf = add_panel((int)gi, b_off, nl, kMmaN);
           gb.kin = add_mblock((int)gi, na_rows, nl, a_off, b_off, pk, pf, -1, 0);
         }
         if (j2) {
           const int b_off = (int)P.pairs.size();
           for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_G + q, -1));
-          const int pg = add_panel((int)gi, b_off, g.nG, 64);
+          const int pg = add_panel((int)gi, b_off, g.nG, kMmaN);
           gb.j2 = add_mblock((int)gi, g.nG, g.nG, u_off, b_off, pu, pg, -1, 0);
         }
       } else if (g.nFA > 0 && g.nFB > 0) {
@@ -660,14 +709,14 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
             for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
           if (mask & PSQ_V) { gb.rowVC = (int)P.pairs.size() - a_off; P.pairs.push_back(make_short2(W + 3, -1)); }
           const int na_rows = (int)P.pairs.size() - a_off;
-          const int pc = add_panel((int)gi, a_off, na_rows, 128);
+          const int pc = add_panel((int)gi, a_off, na_rows, kMmaM);
           const int b_off = (int)P.pairs.size();
           for (int i = 0; i < g.nFA; ++i)
             for (int jj = 0; jj < g.nFB; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + g.nFA + jj));
           std::vector<PairRef> pl;
-          for (int ib = 0; ib < g.nFA; ib += 8)
+          for (int ib = 0; ib < g.nFA; ib += 6)
             for (int jb = 0; jb < g.nFB; jb += 8)
-              for (int i = ib; i < std::min(g.nFA, ib + 8); ++i)
+              for (int i = ib; i < std::min(g.nFA, ib + 6); ++i)
                 for (int jj = jb; jj < std::min(g.nFB, jb + 8); ++jj)
                   pl.push_back(PairRef{i * g.nFB + jj, g.row_F + i, g.row_F + g.nFA + jj});
           const auto tl = add_pair_tiles(pl);
@@ -737,32 +786,45 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
                                     local_off(G, Y), local_off(G, W)};
           }
     }
-    // work items: 128-row x 64-column tiles of every block, its windows cut for load balance
-    int64_t mtiles = 0;
-    for (auto& mb : P.mblocks)
-      mtiles += (int64_t)((mb.m + 127) / 128) * (mb.b_panel >= 0 ? (mb.n + 63) / 64 : mb.n_btiles);
-    // work_split items per SM (16 by default: a static round-robin then ends within ~6% of
-    // the mean), ranges of at least 4 windows
-    const int64_t want = (int64_t)P.work_split * kSmCount;
-    const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
-    for (size_t bi = 0; bi < P.mblocks.size(); ++bi) {
-      MmaBlock& mb = P.mblocks[bi];
-      const int64_t nwin = ((P.grids[mb.grid].K + 63) / 64 + 1) / 2;
-      const int64_t r0 = std::max<int64_t>(1, std::min<int64_t>(cr, (nwin + 3) / 4));
-      mb.win_per = (int)((nwin + r0 - 1) / r0);
-      mb.n_ranges = (int)((nwin + mb.win_per - 1) / mb.win_per);
-      mb.part_off = part;
-      part += (int64_t)mb.n_ranges * mb.m * mb.n;
-      const int tm = (mb.m + 127) / 128, tn = mb.b_panel >= 0 ? (mb.n + 63) / 64 : mb.n_btiles;
-      for (int c = 0; c < mb.n_ranges; ++c)
-        for (int x = 0; x < tm; ++x)
-          for (int y = 0; y < tn; ++y) P.mitems.push_back(GemmItem{(int)bi, x, y, c});
+    // Waves: consecutive grids while their operand rows (hi and lo planes) and packed panels
+    // fit the budget (a wave holds at least one grid).  Offsets of grids, panels and blocks
+    // are then made relative to the wave; the regions are sized by the largest wave.
+    const int nG = (int)P.grids.size();
+    std::vector<int64_t> g_ops(nG, 0), g_bytes(nG, 0);
+    for (int gi = 0; gi < nG; ++gi) {
+      const int64_t end = gi + 1 < nG ? P.grids[gi + 1].op_off : ops;
+      g_ops[gi] = end - P.grids[gi].op_off;
+      g_bytes[gi] = 2 * (int64_t)sizeof(float) * g_ops[gi];
     }
+    auto panel_bytes = [&](const Panel& pn, int64_t* pack, int64_t* expb) {
+      *pack = (int64_t)align_up((size_t)pn.nrows * pn.nch * kSlices * 2 * kChunkPts, 256);
+      *expb = (int64_t)align_up((size_t)pn.n_tiles * pn.nwin * pn.tr * 4, 256);
+    };
+    for (const Panel& pn : P.panels) {
+      int64_t pk, ex;
+      panel_bytes(pn, &pk, &ex);
+      g_bytes[pn.grid] += pk + ex;
+    }
+    const int64_t budget = (int64_t)(j->wave_bytes ? j->wave_bytes : kDefaultWaveBytes);
+    for (int g0 = 0; g0 < nG;) {
+      int g1 = g0;
+      int64_t acc = 0;
+      while (g1 < nG && (g1 == g0 || acc + g_bytes[g1] <= budget)) acc += g_bytes[g1++];
+      Plan::Wave wv{};
+      wv.g0 = g0;
+      wv.g1 = g1;
+      P.waves.push_back(wv);
+      g0 = g1;
+    }
+    int64_t ops_max = 0, pack_max = 0, part_max = 0;
+    size_t pn_i = 0, mb_i = 0;
+    const double kSliceProducts = kSlices * (kSlices + 1) / 2;
+    constexpr int64_t kCpw = kWinPts / kChunkPts;  // chunks per window
     auto item_chunks = [&](const GemmItem& it) {
       const MmaBlock& mb = P.mblocks[it.block];
-      const int64_t nch = (P.grids[mb.grid].K + 63) / 64;
-      const int64_t c0 = 2LL * it.chunk * mb.win_per;
-      return std::max<int64_t>(0, std::min<int64_t>(nch, c0 + 2LL * mb.win_per) - c0);
+      const int64_t nch = (P.grids[mb.grid].K + kChunkPts - 1) / kChunkPts;
+      const int64_t c0 = kCpw * it.chunk * mb.win_per;
+      return std::max<int64_t>(0, std::min<int64_t>(nch, c0 + kCpw * mb.win_per) - c0);
     };
     // Items by estimated cost (chunks; a formed pair tile's window counts twice: its
     // producers' slicing), largest first, each given to the persistent CTA with the least
@@ -770,31 +832,89 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     auto item_cost = [&](const GemmItem& it) {
       return (double)item_chunks(it) * (P.mblocks[it.block].b_panel < 0 ? 2.0 : 1.0);
     };
-    std::stable_sort(P.mitems.begin(), P.mitems.end(),
-                     [&](const GemmItem& x, const GemmItem& y) { return item_cost(x) > item_cost(y); });
-    P.n_ctas = (int)std::min<int64_t>((int64_t)P.mitems.size(), j->ctx->sm_count);
-    {
-      std::vector<std::vector<GemmItem>> per(P.n_ctas);
+    P.cta_begin.clear();
+    for (Plan::Wave& wv : P.waves) {
+      // operand rows of the wave's grids from 0
+      int64_t o = 0;
+      for (int gi = wv.g0; gi < wv.g1; ++gi) {
+        P.grids[gi].op_off = o;
+        o += g_ops[gi];
+      }
+      ops_max = std::max(ops_max, o);
+      // its panels (consecutive, in grid order) packed from 0, packing jobs counted from 0
+      wv.pn0 = (int)pn_i;
+      int64_t pb = 0, jobs = 0;
+      while (pn_i < P.panels.size() && P.panels[pn_i].grid < wv.g1) {
+        Panel& pn = P.panels[pn_i++];
+        int64_t pk, ex;
+        panel_bytes(pn, &pk, &ex);
+        pn.pack_off = pb;
+        pn.exp_off = pb + pk;
+        pb += pk + ex;
+        pn.job_begin = jobs;
+        jobs += (int64_t)pn.n_tiles * pn.nwin * (pn.tr / kPackRows);  // 16-row groups
+      }
+      wv.pn1 = (int)pn_i;
+      wv.jobs = jobs;
+      pack_max = std::max(pack_max, pb);
+      // its blocks: tiles (128 rows x 48 columns) x window ranges, work_split items per SM
+      // (a static LPT deal then ends within a few percent of the mean), ranges of >= 4 windows
+      wv.mb0 = (int)mb_i;
+      while (mb_i < P.mblocks.size() && P.mblocks[mb_i].grid < wv.g1) ++mb_i;
+      wv.mb1 = (int)mb_i;
+      int64_t mtiles = 0;
+      for (int bi = wv.mb0; bi < wv.mb1; ++bi) {
+        const MmaBlock& mb = P.mblocks[bi];
+        mtiles += (int64_t)((mb.m + kMmaM - 1) / kMmaM) * (mb.b_panel >= 0 ? (mb.n + kMmaN - 1) / kMmaN : mb.n_btiles);
+      }
+      const int64_t want = (int64_t)P.work_split * kSmCount;
+      const int cr = (int)std::max<int64_t>(1, mtiles > 0 ? (want + mtiles - 1) / mtiles : 1);
+      std::vector<GemmItem> items;
+      int64_t pt = 0;
+      for (int bi = wv.mb0; bi < wv.mb1; ++bi) {
+        MmaBlock& mb = P.mblocks[bi];
+        const int64_t nwin = (P.grids[mb.grid].K + kWinPts - 1) / kWinPts;
+        const int64_t r0 = std::max<int64_t>(1, std::min<int64_t>(cr, (nwin + 3) / 4));
+        mb.win_per = (int)((nwin + r0 - 1) / r0);
+        mb.n_ranges = (int)((nwin + mb.win_per - 1) / mb.win_per);
+        mb.part_off = pt;
+        pt += (int64_t)mb.n_ranges * mb.m * mb.n;
+        const int tm = (mb.m + kMmaM - 1) / kMmaM, tn = mb.b_panel >= 0 ? (mb.n + kMmaN - 1) / kMmaN : mb.n_btiles;
+        for (int c = 0; c < mb.n_ranges; ++c)
+          for (int x = 0; x < tm; ++x)
+            for (int y = 0; y < tn; ++y) items.push_back(GemmItem{bi, x, y, c});
+      }
+      part_max = std::max(part_max, pt);
+      std::stable_sort(items.begin(), items.end(),
+                       [&](const GemmItem& x, const GemmItem& y) { return item_cost(x) > item_cost(y); });
+      wv.n_ctas = (int)std::min<int64_t>((int64_t)items.size(), j->ctx->sm_count);
+      std::vector<std::vector<GemmItem>> per(wv.n_ctas);
       std::vector<std::pair<double, int>> heap;  // (cost so far, CTA), min-heap
-      for (int b = 0; b < P.n_ctas; ++b) heap.push_back({0.0, b});
+      for (int b = 0; b < wv.n_ctas; ++b) heap.push_back({0.0, b});
       auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x > y; };
       std::make_heap(heap.begin(), heap.end(), cmp);
-      for (const GemmItem& it : P.mitems) {
+      for (const GemmItem& it : items) {
         std::pop_heap(heap.begin(), heap.end(), cmp);
         per[heap.back().second].push_back(it);
         heap.back().first += item_cost(it);
         std::push_heap(heap.begin(), heap.end(), cmp);
       }
-      P.mitems.clear();
-      P.cta_begin.assign(1, 0);
+      wv.cb_off = (int)P.cta_begin.size();
+      P.cta_begin.push_back((int)P.mitems.size());
       for (auto& v : per) {
         P.mitems.insert(P.mitems.end(), v.begin(), v.end());
         P.cta_begin.push_back((int)P.mitems.size());
       }
+      // issued tensor work: per 32-point chunk of an item, the slice products of orders 0..4
+      // (15 of 128 x 48 x 32, issued per 16-point K step as five MMAs of N = 240 .. 48)
+      for (const GemmItem& it : items)
+        P.issued_flops += (double)item_chunks(it) * kSliceProducts * 2.0 * kMmaM * kMmaN * kChunkPts;
     }
-    // issued tensor work: per 64-point chunk of an item, the slice products of orders 0..3
-    // (10 of 128 x 64 x 64, issued as four MMAs of N = 256, 192, 128, 64)
-    for (const GemmItem& it : P.mitems) P.issued_flops += (double)item_chunks(it) * 10.0 * 2.0 * 128.0 * 64.0 * 64.0;
+    P.n_ctas = 0;
+    for (const Plan::Wave& wv : P.waves) P.n_ctas = std::max(P.n_ctas, wv.n_ctas);
+    ops = ops_max;
+    P.pack_bytes = pack_max;
+    part = part_max;
     P.elem_begin.resize(P.mblocks.size() + 1);
     P.elem_begin[0] = 0;
     for (size_t bi = 0; bi < P.mblocks.size(); ++bi)
@@ -803,11 +923,6 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   for (int c = 0; c < 4; ++c) P.src_ptr[c][nat * nat] = (int)P.src[c].size();
   if (P.mixed) {
     // FP32-pair rotation, x-scales of the shells and FP64 row constants
-    auto klm = [](int l, int m) {
-      const int am = std::abs(m);
-      double k = std::sqrt((2 * l + 1) / (4 * M_PI) * factorial(l - am) / factorial(l + am));
-      return m != 0 ? k * std::sqrt(2.0) : k;
-    };
     auto split = [](double v) {
       const float hi = (float)v;
       return make_float2(hi, (float)(v - (double)hi));
@@ -829,34 +944,15 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       int nrows = g.row_W + 4;
       P.rowc.resize(P.rowc.size() + nrows, 1.0);
       double* rc = P.rowc.data() + g.rc_off;
-      auto basis_rows = [&](int row0, double zpow_extra) {
-        int r = row0;
-        for (int c = 0; c < 2; ++c) {
-          const int s0 = c == 0 ? g.shb_A0 : g.shb_B0, s1 = c == 0 ? g.shb_A1 : g.shb_B1;
-          for (int q = s0; q < s1; ++q) {
-            const DevShell& d = j->dbs[q];
-            for (int m = -d.l; m <= d.l; ++m)
-              rc[r++] = d.norm * klm(d.l, m) * std::pow(d.zeta, -(d.n - 1) + zpow_extra);
-          }
-        }
+      auto put_rows = [&](int row0, int kind) {
+        std::vector<double> v;
+        row_constants(j, g, kind, v);
+        for (size_t r = 0; r < v.size(); ++r) rc[row0 + r] = v[r];
       };
-      if (g.row_F >= 0) basis_rows(g.row_F, 0.0);
-      if (g.row_L >= 0) basis_rows(g.row_L, 2.0);
-      auto aux_rows = [&](int row0, bool pot) {
-        int r = row0;
-        for (int c = 0; c < 2; ++c) {
-          const int s0 = c == 0 ? g.sha_0 : g.sha_2, s1 = c == 0 ? g.sha_1 : g.sha_3;
-          if ((c == 0 ? g.aux_c0 : g.aux_c1) < 0) continue;
-          for (int q = s0; q < s1; ++q) {
-            const DevShell& d = j->das[q];
-            for (int m = -d.l; m <= d.l; ++m)
-              rc[r++] = pot ? 4.0 * M_PI / (2 * d.l + 1) * d.norm * klm(d.l, m) * std::pow(d.zeta, -(d.n + 1))
-                            : d.norm * klm(d.l, m) * std::pow(d.zeta, -(d.n - 1));
-          }
-        }
-      };
-      if (g.row_G >= 0) aux_rows(g.row_G, false);
-      if (g.row_U >= 0) aux_rows(g.row_U, true);
+      if (g.row_F >= 0) put_rows(g.row_F, 0);
+      if (g.row_L >= 0) put_rows(g.row_L, 1);
+      if (g.row_G >= 0) put_rows(g.row_G, 2);
+      if (g.row_U >= 0) put_rows(g.row_U, 3);
       rc[g.row_W + 0] = g.a * g.a * g.a;
       rc[g.row_W + 1] = 0.5 * g.a * g.a;
       rc[g.row_W + 2] = 0.5 * g.a * g.a;
@@ -873,6 +969,13 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   }
   for (size_t gi = 0; gi < P.grids.size(); ++gi)
     for (int64_t p0 = 0; p0 < P.grids[gi].K; p0 += kPointsPerBlock) P.pblocks.push_back(PointBlock{(int)gi, 0, p0});
+  for (Plan::Wave& wv : P.waves) {
+    wv.pb0 = wv.pb1 = (int)P.pblocks.size();
+    for (int k = 0; k < (int)P.pblocks.size(); ++k) {
+      if (P.pblocks[k].grid >= wv.g0 && wv.pb0 == (int)P.pblocks.size()) wv.pb0 = k;
+      if (P.pblocks[k].grid >= wv.g1) { wv.pb1 = k; break; }
+    }
+  }
   // useful contractions: for every molecule-matrix block, rows x cols x the live points of
   // the one grid that integrates it (same-atom blocks count i <= j once)
   P.contractions = 0;
@@ -898,7 +1001,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   }
   int nclasses = 0;
   for (int c = 0; c < 5; ++c) nclasses += (mask >> c) & 1;
-  P.launches = P.grids.empty() ? 0 : (P.mixed ? 5 : 3) + nclasses;
+  P.launches = P.grids.empty() ? 0 : (P.mixed ? 1 + 4 * (int)P.waves.size() : 3) + nclasses;
   // table layout
   size_t off = 0;
   auto sec = [&](size_t bytes) {
@@ -937,7 +1040,8 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   P.nodes_off = off;
   off = align_up(off + sizeof(NodeEntry) * (size_t)P.n_nodes, 256);
   P.ops_off = off;
-  off = align_up(off + esize * (size_t)ops, 256);
+  P.n_ops = ops;
+  off = align_up(off + esize * (size_t)ops * (P.mixed ? 2 : 1), 256);
   P.pack_off = off;
   off = align_up(off + (size_t)P.pack_bytes, 256);
   P.part_off = off;
@@ -993,23 +1097,33 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   return PSQ_OK;
 }
 
-psq_status get_plan(psq_job* j, unsigned mask, Plan** out) {
+// The job's plan for mask (made on first use), shared with the caller so that a concurrent
+// psq_job_autotune replacing it cannot free it under a running compute.
+psq_status get_plan_shared(psq_job* j, unsigned mask, std::shared_ptr<Plan>* out) {
   std::lock_guard<std::mutex> lk(j->mu);
   auto it = j->plans.find(mask);
   if (it != j->plans.end()) {
-    *out = it->second.get();
+    *out = it->second;
     return PSQ_OK;
   }
-  std::unique_ptr<Plan> p(new (std::nothrow) Plan());
+  std::shared_ptr<Plan> p(new (std::nothrow) Plan());
   if (!p) return fail(PSQ_ERR_OOM, "plan allocation failed");
   auto ws = j->work_split.find(mask);
   if (ws != j->work_split.end()) p->work_split = ws->second;
   else p->work_split = j->prec == PSQ_MIXED ? 16 : 8;
   psq_status st = make_plan(j, mask, *p);
   if (st != PSQ_OK) return st;
-  *out = p.get();
+  *out = p;
   j->plans[mask] = std::move(p);
   return PSQ_OK;
+}
+
+// The same for queries that only read the plan's sizes while the caller holds the job.
+psq_status get_plan(psq_job* j, unsigned mask, Plan** out) {
+  std::shared_ptr<Plan> sp;
+  psq_status st = get_plan_shared(j, mask, &sp);
+  if (st == PSQ_OK) *out = sp.get();
+  return st;
 }
 
 // Records a timing event before a launch of `kind` (kind -1 closes a psq_compute call).
@@ -1260,6 +1374,8 @@ psq_status psq::set_error(psq_status s, const char* msg) { return fail(s, "%s", 
 
 int psq::context_device(const psq_context* ctx) { return ctx ? ctx->device : -1; }
 
+int psq::job_device(const psq_job* job) { return job && job->ctx ? job->ctx->device : -1; }
+
 size_t psq::status_offset(psq_job* job, unsigned mask) {
   std::lock_guard<std::mutex> lk(job->mu);
   auto it = job->plans.find(mask);
@@ -1267,7 +1383,8 @@ size_t psq::status_offset(psq_job* job, unsigned mask) {
 }
 
 namespace {
-psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_out[5], cudaStream_t s);
+psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_out[5], cudaStream_t s,
+                    bool timing = true);
 }
 
 psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_t ws_bytes, double* d_out[5],
@@ -1279,27 +1396,36 @@ psq_status psq::compute_on(psq_job* job, unsigned mask, void* d_workspace, size_
   if (!d_out) return fail(PSQ_ERR_ARG, "d_out is NULL");
   for (int c = 0; c < 5; ++c)
     if ((mask >> c) & 1 && !d_out[c]) return fail(PSQ_ERR_ARG, "output %d is NULL", c);
-  Plan* P = nullptr;
+  std::shared_ptr<Plan> SP;
   if (plan_must_exist) {
     std::lock_guard<std::mutex> lk(job->mu);
     auto it = job->plans.find(mask);
     if (it == job->plans.end())
       return fail(PSQ_ERR_ARG, "no plan for mask 0x%x yet: call psq_job_workspace(job, mask) first", mask);
-    P = it->second.get();
+    SP = it->second;
   } else {
-    psq_status st = get_plan(job, mask, &P);
+    psq_status st = get_plan_shared(job, mask, &SP);
     if (st != PSQ_OK) return st;
   }
+  Plan* P = SP.get();
   if (!d_workspace || ws_bytes < P->ws_bytes)
     return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->ws_bytes);
   if ((uintptr_t)d_workspace % 256) return fail(PSQ_ERR_ARG, "workspace must be 256-byte aligned");
-  return run_plan(job, P, mask, (char*)d_workspace, d_out, (cudaStream_t)stream);
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != job->ctx->device)
+    return fail(PSQ_ERR_ARG, "device %d is current, the job's context is on device %d", dev, job->ctx->device);
+  // the allocation-free path (plan_must_exist outside a capture) records no timing events:
+  // creating them would allocate
+  return run_plan(job, P, mask, (char*)d_workspace, d_out, (cudaStream_t)stream, !plan_must_exist);
 }
 
 namespace {
 
 // The launch sequence of one psq_compute on plan P (arguments checked by the caller).
-psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_out[5], cudaStream_t s) {
+psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_out[5], cudaStream_t s,
+                    bool timing) {
+  auto mark = [&](psq_job* j, int kind, cudaStream_t st) { return timing ? ::mark(j, kind, st) : cudaSuccess; };
   CUDA_TRY(mark(job, 0, s));
   CUDA_TRY(cudaMemcpyAsync(ws, P->staging, P->table_bytes, cudaMemcpyHostToDevice, s));
   const LaunchTables t = tables_at(*P, ws);
@@ -1307,22 +1433,30 @@ psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_ou
   double* res = (double*)(ws + P->res_off);
   if (P->mixed) {
     float* ops = (float*)(ws + P->ops_off);
+    float* ops_lo = ops + P->n_ops;
     NodeEntry* nodes = (NodeEntry*)(ws + P->nodes_off);
+    uint8_t* packed = (uint8_t*)(ws + P->pack_off);
+    const Panel* panels = (const Panel*)(ws + P->o_pn);
     CUDA_TRY(mark(job, 1, s));
     CUDA_TRY(launch_nodes(t.grids, (int)P->grids.size(), P->max_node_entries, t.edges, nodes, s));
-    CUDA_TRY(launch_eval_mixed(t, nodes, (const float2*)(ws + P->o_xi), ops, s));
-    CUDA_TRY(mark(job, 5, s));
-    uint8_t* packed = (uint8_t*)(ws + P->pack_off);
-    CUDA_TRY(launch_pack(t.grids, (const Panel*)(ws + P->o_pn), (int)P->panels.size(), P->n_pack_jobs, t.pairs, ops,
-                         packed, s));
-    CUDA_TRY(mark(job, 2, s));
-    CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
-                                (const int*)(ws + P->o_cb), P->n_ctas, (const Panel*)(ws + P->o_pn),
-                                (const PairTile*)(ws + P->o_pt), ops, packed, (float2*)part,
-                                (int*)(ws + P->o_status), s));
-    CUDA_TRY(mark(job, 3, s));
-    CUDA_TRY(launch_reduce_mixed(t.grids, (const MmaBlock*)(ws + P->o_mb), (int)P->mblocks.size(), t.elem_begin,
-                                 t.n_elems, t.pairs, (const double*)(ws + P->o_rc), (const float2*)part, res, s));
+    for (const Plan::Wave& wv : P->waves) {
+      LaunchTables tw = t;
+      tw.pblocks = t.pblocks + wv.pb0;
+      tw.n_pblocks = wv.pb1 - wv.pb0;
+      CUDA_TRY(mark(job, 1, s));
+      CUDA_TRY(launch_eval_mixed(tw, nodes, (const float2*)(ws + P->o_xi), ops, ops_lo, s));
+      CUDA_TRY(mark(job, 5, s));
+      CUDA_TRY(launch_pack(t.grids, panels + wv.pn0, wv.pn1 - wv.pn0, wv.jobs, t.pairs, ops, ops_lo, packed, s));
+      CUDA_TRY(mark(job, 2, s));
+      CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
+                                  (const int*)(ws + P->o_cb) + wv.cb_off, wv.n_ctas, panels,
+                                  (const PairTile*)(ws + P->o_pt), ops, ops_lo, packed, (float2*)part,
+                                  (int*)(ws + P->o_status), job->wait_ns, s));
+      CUDA_TRY(mark(job, 3, s));
+      CUDA_TRY(launch_reduce_mixed(t.grids, (const MmaBlock*)(ws + P->o_mb), (int)P->mblocks.size(), t.elem_begin,
+                                   P->elem_begin[wv.mb0], P->elem_begin[wv.mb1], t.pairs,
+                                   (const double*)(ws + P->o_rc), (const float2*)part, res, s));
+    }
   } else {
     double* ops = (double*)(ws + P->ops_off);
     CUDA_TRY(mark(job, 1, s));
@@ -1383,11 +1517,11 @@ psq_status psq_job_autotune(psq_job* job, unsigned mask, void* d_workspace, size
   }
   const bool prof = job->prof_on;
   job->prof_on = false;  // the trial runs stay out of the launch timing record
-  std::unique_ptr<Plan> best;
+  std::shared_ptr<Plan> best;
   float best_t = 0.0f;
   psq_status st = PSQ_OK;
   for (int k = 0; k < n_cand && st == PSQ_OK; ++k) {
-    std::unique_ptr<Plan> p(new (std::nothrow) Plan());
+    std::shared_ptr<Plan> p(new (std::nothrow) Plan());
     if (!p) { st = fail(PSQ_ERR_OOM, "plan allocation failed"); break; }
     p->work_split = cand[k];
     st = make_plan(job, mask, *p);
@@ -1479,6 +1613,23 @@ psq_status psq_compute_graph(psq_job* job, unsigned mask, void* d_workspace, siz
   return PSQ_OK;
 }
 
+psq_status psq_job_set_wave_budget(psq_job* job, size_t bytes) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  std::lock_guard<std::mutex> lk(job->mu);
+  job->wave_bytes = bytes;
+  job->plans.clear();
+  for (auto& kv : job->graphs) cudaGraphExecDestroy(kv.second);
+  job->graphs.clear();
+  return PSQ_OK;
+}
+
+psq_status psq_job_set_wait_limit(psq_job* job, uint64_t ns) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  if (ns < 1 || ns > 60000000000ull) return fail(PSQ_ERR_ARG, "wait limit %llu ns out of range", (unsigned long long)ns);
+  job->wait_ns = ns;
+  return PSQ_OK;
+}
+
 psq_status psq_profile_enable(psq_job* job, int on) {
   if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
   job->prof_on = on != 0;
@@ -1540,10 +1691,14 @@ psq_status psq_compute_host(psq_job* job, unsigned mask, void* d_workspace, size
 }
 
 psq_status psq_check(psq_job* job, unsigned mask, void* d_workspace, void* stream) {
-  if (!job || !d_workspace) return fail(PSQ_ERR_ARG, "NULL argument");
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
   Plan* P = nullptr;
   psq_status st = get_plan(job, mask, &P);
   if (st != PSQ_OK) return st;
+  if (!d_workspace) {  // the allocation-free entry point's scratch on the current device
+    st = psq::noalloc_scratch(&d_workspace);
+    if (st != PSQ_OK) return st;
+  }
   int flag = 0;
   cudaStream_t s = (cudaStream_t)stream;
   CUDA_TRY(cudaMemcpyAsync(&flag, (char*)d_workspace + P->o_status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1593,10 +1748,9 @@ psq_status psq_job_grid_functions(psq_job* job, int g, int kind, void* d_workspa
   psq_status st = get_plan(job, PSQ_ALL, &P);
   if (st != PSQ_OK) return st;
   if (g < 0 || g >= (int)P->grids.size()) return fail(PSQ_ERR_ARG, "grid %d of %zu", g, P->grids.size());
-  // one-grid table: the grid with only the requested rows, written straight into d_out
+  // one-grid table: the grid with only the requested rows
   DevGrid G = P->grids[g];
   G.op_off = 0;
-  G.ld = G.K;
   G.row_F = G.row_L = G.row_G = G.row_U = G.row_W = -1;
   int nrows = kind <= 1 ? G.nFA + G.nFB : G.nG;
   if (kind == 0) G.row_F = 0;
@@ -1604,10 +1758,22 @@ psq_status psq_job_grid_functions(psq_job* job, int g, int kind, void* d_workspa
   if (kind == 2) G.row_G = 0;
   if (kind == 3) G.row_U = 0;
   if (rows) *rows = nrows;
+  const bool mixed = job->prec == PSQ_MIXED;
   std::vector<PointBlock> pb;
   for (int64_t p0 = 0; p0 < G.K; p0 += kPointsPerBlock) pb.push_back(PointBlock{0, 0, p0});
+  // mixed path: node table of this grid, the FP64 row constants and the hi/lo operand rows
+  const int n_nodes = (G.n_mu + G.nt_mu * G.n_sp) * G.q_mu + (G.n_nu + G.nt_nu * G.n_sp) * G.q_nu +
+                      (G.n_phi + G.nt_phi * G.n_sp) * G.q_phi;
+  std::vector<double> rc;
+  if (mixed) row_constants(job, G, kind, rc);
+  G.ld = mixed ? (int64_t)align_up((size_t)G.K, 128) : G.K;
+  if (mixed) G.nt_off = 0;
   const size_t o_grid = 0, o_pb = align_up(sizeof(DevGrid), 256);
-  const size_t need = o_pb + align_up(sizeof(PointBlock) * pb.size(), 256);
+  size_t need = o_pb + align_up(sizeof(PointBlock) * pb.size(), 256);
+  const size_t o_nodes = need;
+  const size_t o_rc = o_nodes + (mixed ? align_up(sizeof(NodeEntry) * (size_t)n_nodes, 256) : 0);
+  const size_t o_ops = o_rc + (mixed ? align_up(sizeof(double) * rc.size(), 256) : 0);
+  if (mixed) need = o_ops + align_up(2 * sizeof(float) * (size_t)nrows * (size_t)G.ld, 256);
   if (!d_workspace || ws_bytes < P->table_bytes + need)
     return fail(PSQ_ERR_OOM, "workspace of %zu bytes given, %zu needed", ws_bytes, P->table_bytes + need);
   cudaStream_t s = (cudaStream_t)stream;
@@ -1620,7 +1786,18 @@ psq_status psq_job_grid_functions(psq_job* job, int g, int kind, void* d_workspa
   t.grids = (const DevGrid*)(extra + o_grid);
   t.pblocks = (const PointBlock*)(extra + o_pb);
   t.n_pblocks = (int)pb.size();
-  CUDA_TRY(launch_eval_fp64(t, d_out, 0, s));
+  if (mixed) {
+    if (!rc.empty())
+      CUDA_TRY(cudaMemcpyAsync(extra + o_rc, rc.data(), sizeof(double) * rc.size(), cudaMemcpyHostToDevice, s));
+    NodeEntry* nodes = (NodeEntry*)(extra + o_nodes);
+    float* oh = (float*)(extra + o_ops);
+    float* ol = oh + (size_t)nrows * G.ld;
+    CUDA_TRY(launch_nodes(t.grids, 1, n_nodes, t.edges, nodes, s));
+    CUDA_TRY(launch_eval_mixed(t, nodes, (const float2*)(ws + P->o_xi), oh, ol, s));
+    CUDA_TRY(launch_combine_rows(oh, ol, (const double*)(extra + o_rc), nrows, G.K, G.ld, d_out, s));
+  } else {
+    CUDA_TRY(launch_eval_fp64(t, d_out, 0, s));
+  }
   CUDA_TRY(cudaStreamSynchronize(s));  // the host copies above live on this stack frame
   return PSQ_OK;
 }

@@ -50,9 +50,13 @@ struct DevGrid {
   int rc_off;          // FP64 constant of every operand row (norms, zeta powers, a^3 ...)
 };
 
-// One Gauss-Legendre node of one dimension of one grid row (FP64): the coordinate v, its
-// sine/cosine (sinh/cosh for mu), sin^2(v/2) (sinh^2 for mu), cos^2(v/2), and the 1-D weight.
-struct NodeEntry { double v, s, c, h2, g2, w; };
+// One Gauss-Legendre node of one dimension of one grid row: the coordinate v and its
+// sine/cosine (sinh/cosh for mu) in FP64 (third-centre offsets), and as double-float (hi, lo)
+// pairs the sine/cosine, sin^2(v/2) (sinh^2 for mu), cos^2(v/2) and the 1-D weight.
+struct NodeEntry {
+  double v, s, c;
+  float2 fs, fc, fh2, fg2, fw;
+};
 
 // A contraction block of the tensor-core path: R[r][c] = sum_p A_r(p) B_c(p), row-major
 // m x n, where every operand row is one of the grid's operand rows times an optional second
@@ -70,35 +74,45 @@ struct MmaBlock {
   int64_t res_off, part_off;
 };
 
+// Tensor-core tiling of the mixed path (shared by the planner and the kernels).
+constexpr int kMmaM = 128;     // tile rows
+constexpr int kMmaN = 48;      // tile columns: 5 orders x 48 columns x 2 accumulator sets fill 480 of
+                               // the 512 TMEM columns
+constexpr int kChunkPts = 32;  // points per shared-memory stage (one 64-byte row of BF16 digits)
+constexpr int kWinPts = 128;   // points per scale window (the exact FP32 accumulation bound)
+constexpr int kSlices = 5;     // 8-bit integer slices per operand value; orders 0..4 are kept
+constexpr int kPackRows = 16;  // operand rows per packing job
+
 // A packed operand panel: nrows operand rows (rows[rows_off ...]) of one grid in tiles of tr
-// rows (128 for the A side of a tile, 64 for B); tile t holds rt = min(tr, nrows - t*tr) rows.
-// Every value is split into four BF16 planes of 8-bit integers under a power-of-two scale
-// per row and 128-point window (exponent e: value = 2^(e-7) (s0 + s1/256 + s2/256^2 +
-// s3/256^3)).  The planes of tile t, 64-point chunk c start at pack_off + t*nch*4*tr*128 +
-// c*4*rt*128 bytes, plane k rt*128 bytes after plane k-1, each exactly as the tcgen05
-// shared-memory operand wants it: 128-byte rows (64 points), the eight 16-byte groups of row
-// r XOR-swizzled by r % 8.  Rows past rt are not stored (their products only reach result
-// rows or columns that are never read).  The exponents of tile t, window w are tr ints at
-// exp_off + (t*nwin + w)*tr*4 bytes; a zero row (or padding row) has exponent kZeroExp.
+// rows (kMmaM for the A side of a tile, kMmaN for B); tile t holds rt = min(tr, nrows - t*tr)
+// rows.  Every value is split into kSlices BF16 planes of 8-bit integers under a power-of-two
+// scale per row and kWinPts-point window (exponent e: value = 2^(e-7) (s0 + s1/256 + ... +
+// s4/256^4)).  The planes of tile t, 32-point chunk c start at pack_off + t*nch*5*tr*64 +
+// c*5*rt*64 bytes, plane k rt*64 bytes after plane k-1, each exactly as the tcgen05
+// shared-memory operand wants it: 64-byte rows (32 points), the four 16-byte groups of row r
+// XOR-swizzled by (r / 2) % 4 (the 64-byte swizzle).  Rows past rt are not stored (their
+// products only reach result rows or columns that are never read).  The exponents of tile t,
+// window w are tr ints at exp_off + (t*nwin + w)*tr*4 bytes; a zero row (or padding row) has
+// exponent kZeroExp.
 struct Panel {
   int grid;
   int rows_off, nrows;
   int tr, n_tiles;
   int nch, nwin;
   int64_t pack_off, exp_off;
-  int64_t job_begin;  // first packing job (tile, window, 64-row group) of this panel, prefix over panels
+  int64_t job_begin;  // first packing job (tile, window, 16-row group) of this panel, prefix over panels
 };
 constexpr int kZeroExp = -100000;
 
-// The formed B operand of one 64-column tile of a 3-index block: column c is the product of
+// The formed B operand of one tile of a 3-index block: column c (< kMmaN) is the product of
 // the staged basis rows dx[c] and dy[c] (indices into rows[], grid operand rows) and lands
 // in column col[c] of the block's result.
-constexpr int kPairTileRows = 24;
+constexpr int kPairTileRows = 16;
 struct PairTile {
   int ncols, nrows;
   short rows[kPairTileRows];
-  unsigned char dx[64], dy[64];
-  int col[64];
+  unsigned char dx[kMmaN], dy[kMmaN];
+  int col[kMmaN];
 };
 
 // One output block of a contraction (eq 9): out[r][c] = sum_p A_r(p) d(p) B_c(p), where
@@ -169,21 +183,26 @@ void upload_mixed_tables(const double* x, const double* w, const double* klm);
 cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, const double* edges, NodeEntry* tab,
                          cudaStream_t s);
 cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const float2* xi, float* ops,
-                              cudaStream_t s);
+                              float* ops_lo, cudaStream_t s);
+cudaError_t launch_combine_rows(const float* h, const float* l, const double* rc, int nrows, int64_t K, int64_t ld,
+                                double* out, cudaStream_t s);
 size_t ws_smem_bytes();
 cudaError_t prepare_kernels();  // per-device kernel attributes (context creation)
 cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
-                        const float* ops, uint8_t* packed, cudaStream_t s);
+                        const float* ops, const float* ops_lo, uint8_t* packed, cudaStream_t s);
 // Packed panels of the RI 4-index product from FP64 rows (panels[0] from srcA, panels[1] from
 // srcB, rows of n values); n_jobs covers both panels' packing jobs.
 cudaError_t launch_ri_pack(const Panel* panels, int64_t n_jobs, const double* srcA, const double* srcB, int n,
                            uint8_t* packed, cudaStream_t s);
 // CTA b of the persistent contraction works through items [cta_begin[b], cta_begin[b + 1]).
+// wait_ns bounds every wait of the main loops (the drains after a timeout keep a fixed 4 s).
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items,
                                const int* cta_begin, int n_ctas, const Panel* panels, const PairTile* ptiles,
-                               const float* ops, const uint8_t* packed, float2* part, int* status, cudaStream_t s);
+                               const float* ops, const float* ops_lo, const uint8_t* packed, float2* part, int* status,
+                               uint64_t wait_ns, cudaStream_t s);
+// Reduces the elements [e0, e1) of the blocks (prefix sums elem_begin).
 cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
-                                int64_t n_elems, const short2* rows, const double* rowc, const float2* part,
+                                int64_t e0, int64_t e1, const short2* rows, const double* rowc, const float2* part,
                                 double* res, cudaStream_t s);
 
 // Host side (psq_host.cpp): psq_compute on a given workspace; with plan_must_exist the call
@@ -192,5 +211,9 @@ psq_status compute_on(psq_job* job, unsigned mask, void* d_workspace, size_t ws_
                       void* stream, bool plan_must_exist);
 psq_status set_error(psq_status s, const char* msg);
 int context_device(const psq_context* ctx);           // -1 for a planning-only context
+int job_device(const psq_job* job);                   // the device of the job's context
+// Device address of the allocation-free entry point's scratch on the current device (looked
+// up once per device).
+psq_status noalloc_scratch(void** ptr);
 size_t status_offset(psq_job* job, unsigned mask);     // workspace offset of the status word
 }  // namespace psq

@@ -22,9 +22,11 @@
 //    FP64 constants of each row and column (normalisations, powers of zeta, a^3), which the
 //    FP32 values omit.
 #include "psq_internal.h"
+#include "psq_df.cuh"
 
 #include <cuda_bf16.h>
 
+#include <cmath>
 #include <cstdint>
 
 namespace psq {
@@ -33,28 +35,44 @@ namespace psq {
 
 __constant__ double c_glx2[kMaxQ + 1][kMaxQ];
 __constant__ double c_glw2[kMaxQ + 1][kMaxQ];
-__constant__ float c_klmf[(kMaxL + 1) * (kMaxL + 1)];
-__constant__ float c_factf[2 * kMaxN + 4];
-__constant__ float c_rcpf[128];  // 1/n
+__constant__ float c_rcpf[128];           // 1/n (FP32 tails of the incomplete-gamma series)
+__constant__ float2 c_factd[2 * kMaxN + 4];  // k! as (hi, lo)
+__constant__ float2 c_exp_tab[64];        // 2^(-j/64) as (hi, lo)
+__constant__ dfa::ExpConsts c_expc;
+
+__host__ __device__ __forceinline__ float2 split_f(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
 
 void upload_mixed_tables(const double* x, const double* w, const double* klm) {
+  (void)klm;
   cudaMemcpyToSymbol(c_glx2, x, sizeof(double) * (kMaxQ + 1) * kMaxQ);
   cudaMemcpyToSymbol(c_glw2, w, sizeof(double) * (kMaxQ + 1) * kMaxQ);
-  float k[(kMaxL + 1) * (kMaxL + 1)];
-  for (int i = 0; i < (kMaxL + 1) * (kMaxL + 1); ++i) k[i] = (float)klm[i];
-  cudaMemcpyToSymbol(c_klmf, k, sizeof(k));
-  float f[2 * kMaxN + 4];
+  float2 f[2 * kMaxN + 4];
   double fd = 1.0;
-  f[0] = 1.0f;
+  f[0] = split_f(1.0);
   for (int i = 1; i < 2 * kMaxN + 4; ++i) {
     fd *= i;
-    f[i] = (float)fd;
+    f[i] = split_f(fd);
   }
-  cudaMemcpyToSymbol(c_factf, f, sizeof(f));
+  cudaMemcpyToSymbol(c_factd, f, sizeof(f));
   float r[128];
   r[0] = 0.0f;
   for (int i = 1; i < 128; ++i) r[i] = (float)(1.0 / i);
   cudaMemcpyToSymbol(c_rcpf, r, sizeof(r));
+  float2 t[64];
+  for (int j = 0; j < 64; ++j) t[j] = split_f(std::exp2(-j / 64.0));
+  cudaMemcpyToSymbol(c_exp_tab, t, sizeof(t));
+  // ln2/64 = c1 + c2 + c3, c1 rounded to 10 significant bits
+  const double l64 = 0.693147180559945309417232121458 / 64.0;
+  int e2 = 0;
+  std::frexp(l64, &e2);
+  const double c1 = std::ldexp(std::nearbyint(std::ldexp(l64, 10 - e2)), e2 - 10);
+  const float c2 = (float)(l64 - c1);
+  const float c3 = (float)(l64 - c1 - (double)c2);
+  dfa::ExpConsts ec{(float)(64.0 / 0.693147180559945309417232121458), (float)c1, c2, c3};
+  cudaMemcpyToSymbol(c_expc, &ec, sizeof(ec));
 }
 
 // Entry (row, node) of one dimension: rows 0..N-1 are the volume-element rows, then
@@ -93,138 +111,72 @@ __global__ void nodes_kernel(const DevGrid* __restrict__ grids, const double* __
   }
   const double h = 0.5 * (m1 - m0);
   const double v = 0.5 * (m0 + m1) + h * c_glx2[Q][q];
-  NodeEntry o;
-  o.v = v;
-  o.w = h * c_glw2[Q][q];
+  double s, c, h2, g2;
   if (dim == 0) {
-    o.s = sinh(v);
-    o.c = cosh(v);
+    s = sinh(v);
+    c = cosh(v);
     const double sh2 = sinh(0.5 * v);
-    o.h2 = sh2 * sh2;
-    o.g2 = 0.0;
+    h2 = sh2 * sh2;
+    g2 = 0.0;
   } else {
-    sincos(v, &o.s, &o.c);
+    sincos(v, &s, &c);
     double s2, c2;
     sincos(0.5 * v, &s2, &c2);
-    o.h2 = s2 * s2;
-    o.g2 = c2 * c2;
+    h2 = s2 * s2;
+    g2 = c2 * c2;
   }
+  NodeEntry o;
+  o.v = v;
+  o.s = s;
+  o.c = c;
+  o.fs = split_f(s);
+  o.fc = split_f(c);
+  o.fh2 = split_f(h2);
+  o.fg2 = split_f(g2);
+  o.fw = split_f(h * c_glw2[Q][q]);
   tab[g.nt_off + e] = o;
 }
 
 // ------------------------------------------------------------------ mixed evaluation
+//
+// Every value is a double-float (hi, lo) pair (about 48 bits): the slices the contraction
+// keeps reach 39 bits of each 128-point window's largest value, so the function values must
+// carry more than that.
 
-// Unnormalised real harmonics Yu_lm(u) = Q_l^|m|(u_z) {Re, Im}(u_x + i u_y)^|m| (the norms K_lm
-// are applied in FP64 with the other row constants), index l*l + l + m.
-__device__ __forceinline__ void real_ylm_u(int lmax, float ux, float uy, float uz, float* Y) {
-  float C[kMaxL + 1], S[kMaxL + 1];
-  C[0] = 1.0f; S[0] = 0.0f;
-  for (int m = 1; m <= lmax; ++m) {
-    C[m] = ux * C[m - 1] - uy * S[m - 1];
-    S[m] = ux * S[m - 1] + uy * C[m - 1];
-  }
-  float dfact = 1.0f;
-  for (int m = 0; m <= lmax; ++m) {
-    if (m > 0) dfact *= (float)(2 * m - 1);
-    float q2 = 0.0f, q1 = dfact;
-    for (int l = m; l <= lmax; ++l) {
-      float q;
-      if (l == m) q = dfact;
-      else if (l == m + 1) q = (float)(2 * m + 1) * uz * dfact;
-      else q = ((float)(2 * l - 1) * uz * q1 - (float)(l + m - 1) * q2) * c_rcpf[l - m];
-      if (l > m) { q2 = q1; q1 = q; }
-      const int base = l * l + l;
-      if (m == 0) {
-        Y[base] = q;
-      } else {
-        Y[base + m] = q * C[m];
-        Y[base - m] = q * S[m];
-      }
-    }
-  }
-}
+using dfa::df;
 
-__device__ __forceinline__ float ipowf(float x, int n) {
-  float r = 1.0f;
-  for (int i = 0; i < n; ++i) r *= x;
-  return r;
-}
+__device__ __forceinline__ df ld2(float2 v) { return df{v.x, v.y}; }
 
-// Radial factors as functions of x = zeta r (row constants carry the powers of zeta):
-//   chi: x^(n-1) e^-x;  lap chi: [(n(n-1) - l(l+1))/x^2 - 2n/x + 1] x^(n-1) e^-x;
-//   V^P: gamma(n+l+2, x)/x^(l+1) + Gamma(n-l+1, x) x^l.
-// x = xh + xl (FP32 pair); the result is corrected to first order in xl.
-__device__ __forceinline__ float radial_x_e(int kind, int n, int l, float xh, float xl, float ex, float ix) {
-  if (kind == 2) {
-    const int k1 = n + l + 2, k2 = n - l + 1;
-    float inner;
-    if (xh < (float)k1) {
-      float term = c_rcpf[k1], sum = term;
-      for (int i = 1; i < 120 - k1; ++i) {
-        term *= xh * c_rcpf[k1 + i];
-        sum += term;
-        if (term <= 3e-8f * sum) break;
-      }
-      inner = ipowf(xh, n + 1) * ex * sum;
-    } else {
-      float t = 1.0f, s = 1.0f;
-      for (int j = 1; j < k1; ++j) { t *= xh * c_rcpf[j]; s += t; }
-      const float f = c_factf[k1 - 1];
-      inner = (f - f * ex * s) * ipowf(ix, l + 1);
-    }
-    float t = 1.0f, s = 1.0f;
-    for (int j = 1; j < k2; ++j) { t *= xh * c_rcpf[j]; s += t; }
-    const float outer = c_factf[k2 - 1] * ex * s * ipowf(xh, l);
-    const float dh = ((float)l * outer - (float)(l + 1) * inner) * ix;  // dh/dx
-    return fmaf(xl, dh, inner + outer);
-  }
-  const float g = ipowf(xh, n - 1) * ex;
-  const float gc = g * fmaf(xl, (float)(n - 1) * ix - 1.0f, 1.0f);
-  if (kind == 0) return gc;
-  const float A = (float)(n * (n - 1) - l * (l + 1));
-  const float f = fmaf(fmaf(A, ix, -2.0f * n), ix, 1.0f);
-  const float df = (2.0f * n - 2.0f * A * ix) * ix * ix;
-  return fmaf(xl, df, f) * gc;
-}
-
-__device__ __forceinline__ float radial_x(int kind, int n, int l, float xh, float xl) {
-  return radial_x_e(kind, n, l, xh, xl, expf(-xh), 1.0f / xh);
-}
-
-// Rows of the shells [s0, s1) of one centre: kind 0 chi, 1 lap chi, 2 V^P.  xi[k] is the
-// (hi, lo) FP32 pair of the scale that turns rho into x for shell s0 + k.
-__device__ __forceinline__ void eval_shells_x(const DevShell* __restrict__ sh, const float2* __restrict__ xi,
-                                              int s0, int s1, float rho, const float* Y, float* __restrict__ out,
-                                              int64_t ld, int64_t p, int row0, int kind) {
+// Rows of the shells [s0, s1) of one centre for one or two row kinds (chi with lap chi, or
+// chi with V^P: x, e^-x and 1/x are shared).  xi[k] is the (hi, lo) scale that turns rho into
+// x for shell s0 + k.  Values go to the hi and lo planes.
+__device__ __forceinline__ void eval_shells_df(const DevShell* __restrict__ sh, const float2* __restrict__ xi,
+                                               int s0, int s1, df rho, const df* Y, float* __restrict__ oh,
+                                               float* __restrict__ ol, int64_t ld, int64_t p, int row_a,
+                                               int kind_a, int row_b, int kind_b, const float2* etab) {
   for (int s = s0; s < s1; ++s) {
     const DevShell q = sh[s];
-    const float2 z = xi[s - s0];
-    const float xh = z.x * rho;
-    const float xl = fmaf(z.x, rho, -xh) + z.y * rho;
-    const float radial = radial_x(kind, q.n, q.l, xh, xl);
+    const df x = dfa::mul(ld2(xi[s - s0]), rho);
+    const df ex = dfa::exp_neg(x, c_expc, etab);
+    const df ix = (kind_a != 0 || (row_b >= 0 && kind_b != 0)) ? dfa::rcp(x) : dfa::mk(0.0f);
     const int base = q.l * q.l + q.l;
-    for (int m = -q.l; m <= q.l; ++m) out[(int64_t)(row0 + q.fn0 + q.l + m) * ld + p] = radial * Y[base + m];
-  }
-}
-
-// The same for two row kinds of the same shells (chi and lap chi, or chi and V^P) at once:
-// x, e^-x and 1/x are shared.
-__device__ __forceinline__ void eval_shells_x2(const DevShell* __restrict__ sh, const float2* __restrict__ xi,
-                                               int s0, int s1, float rho, const float* Y, float* __restrict__ out,
-                                               int64_t ld, int64_t p, int row_a, int kind_a, int row_b,
-                                               int kind_b) {
-  for (int s = s0; s < s1; ++s) {
-    const DevShell q = sh[s];
-    const float2 z = xi[s - s0];
-    const float xh = z.x * rho;
-    const float xl = fmaf(z.x, rho, -xh) + z.y * rho;
-    const float ex = expf(-xh), ix = 1.0f / xh;
-    const float ra = radial_x_e(kind_a, q.n, q.l, xh, xl, ex, ix);
-    const float rb = radial_x_e(kind_b, q.n, q.l, xh, xl, ex, ix);
-    const int base = q.l * q.l + q.l;
-    for (int m = -q.l; m <= q.l; ++m) {
-      out[(int64_t)(row_a + q.fn0 + q.l + m) * ld + p] = ra * Y[base + m];
-      out[(int64_t)(row_b + q.fn0 + q.l + m) * ld + p] = rb * Y[base + m];
+    if (row_a >= 0) {
+      const df ra = dfa::radial(kind_a, q.n, q.l, x, ex, ix, c_factd, c_rcpf);
+      for (int m = -q.l; m <= q.l; ++m) {
+        const df v = dfa::mul(ra, Y[base + m]);
+        const int64_t o = (int64_t)(row_a + q.fn0 + q.l + m) * ld + p;
+        oh[o] = v.h;
+        ol[o] = v.l;
+      }
+    }
+    if (row_b >= 0) {
+      const df rb = dfa::radial(kind_b, q.n, q.l, x, ex, ix, c_factd, c_rcpf);
+      for (int m = -q.l; m <= q.l; ++m) {
+        const df v = dfa::mul(rb, Y[base + m]);
+        const int64_t o = (int64_t)(row_b + q.fn0 + q.l + m) * ld + p;
+        oh[o] = v.h;
+        ol[o] = v.l;
+      }
     }
   }
 }
@@ -235,27 +187,33 @@ __device__ __forceinline__ int shells_lmax_f(const DevShell* sh, int s0, int s1)
   return l;
 }
 
-// v -> R v with R held as an FP32 pair (hi + lo); returns |Rv| and the unit vector.
-__device__ __forceinline__ float rotate_unit(const DevGrid& g, float vx, float vy, float vz, float* u) {
-  float d[3];
+// u = R v / len (R as a double-float matrix), the unit vector of the offset v of length len.
+__device__ __forceinline__ void rotate_unit_df(const DevGrid& g, df vx, df vy, df vz, df inv_len, df* u) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const float hi = fmaf(g.Rh[c * 3], vx, fmaf(g.Rh[c * 3 + 1], vy, g.Rh[c * 3 + 2] * vz));
-    const float lo = fmaf(g.Rl[c * 3], vx, fmaf(g.Rl[c * 3 + 1], vy, g.Rl[c * 3 + 2] * vz));
-    d[c] = hi + lo;
+    const df r0{g.Rh[c * 3], g.Rl[c * 3]}, r1{g.Rh[c * 3 + 1], g.Rl[c * 3 + 1]}, r2{g.Rh[c * 3 + 2], g.Rl[c * 3 + 2]};
+    const df d = dfa::add(dfa::add(dfa::mul(r0, vx), dfa::mul(r1, vy)), dfa::mul(r2, vz));
+    u[c] = dfa::mul(d, inv_len);
   }
-  const float n2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
-  const float inv = rsqrtf(n2);
-  u[0] = d[0] * inv; u[1] = d[1] * inv; u[2] = d[2] * inv;
-  return n2 * inv;
+}
+
+__device__ __forceinline__ df split_d(double v) {
+  const float hi = (float)v;
+  return df{hi, (float)(v - (double)hi)};
 }
 
 // One thread per point.  The weight w = a^3 [G G G sinh mu sin nu (sinh^2 mu + sin^2 nu)]
 // and r_A = 2a rho_A, r_B = 2a rho_B are written without their per-grid constants (a^3,
-// a^2/2), which are applied in FP64 after the contraction; functions likewise.
+// a^2/2), which are applied in FP64 after the contraction; functions likewise.  The offsets
+// from A and B (in units of a) are (sinh mu sin nu cos phi, sinh mu sin nu sin phi,
+// 2(sinh^2(mu/2) cos nu -+ {sin^2, cos^2}(nu/2))), of length 2 rho; the offset from a third
+// centre is formed in FP64 (it cancels near that centre).
 __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const NodeEntry* __restrict__ tab,
                                                          const float2* __restrict__ xi_tab,
-                                                         float* __restrict__ ops) {
+                                                         float* __restrict__ ops, float* __restrict__ ops_lo) {
+  __shared__ float2 etab[64];
+  if (threadIdx.x < 64) etab[threadIdx.x] = c_exp_tab[threadIdx.x];
+  __syncthreads();
   const PointBlock pb = t.pblocks[blockIdx.x];
   const DevGrid& g = t.grids[pb.grid];
   const int p = (int)pb.p0 + (int)threadIdx.x;  // K < 2^31 - 256 (the planner checks)
@@ -293,53 +251,57 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
   const int qj = qnp - qi * g.q_nu;
   const int nmu = (g.n_mu + g.nt_mu * g.n_sp) * g.q_mu;
   const int nnu = (g.n_nu + g.nt_nu * g.n_sp) * g.q_nu;
-  const NodeEntry Mu = tab[g.nt_off + ri * g.q_mu + qi];
-  const NodeEntry Nu = tab[g.nt_off + nmu + rj * g.q_nu + qj];
-  const NodeEntry Ph = tab[g.nt_off + nmu + nnu + rk * g.q_phi + qk];
-  const float sh = (float)Mu.s, s2m = (float)Mu.h2;
-  const float sn = (float)Nu.s, cs = (float)Nu.c, s2n = (float)Nu.h2, c2n = (float)Nu.g2;
-  const float sp = (float)Ph.s, cp = (float)Ph.c;
-  const float w = dead ? 0.0f : (float)(Mu.w * Nu.w * Ph.w) * sh * sn * fmaf(sh, sh, sn * sn);
-  const float rhoA = s2m + s2n, rhoB = s2m + c2n;
-  // pair-frame offsets from A and B, in units of a: (sh sn cos phi, sh sn sin phi, 2(s2m cs -+ ...))
-  const float xs = sh * sn * cp, ys = sh * sn * sp;
-  float uA[3], uB[3], uC[3] = {0.f, 0.f, 1.f};
-  rotate_unit(g, xs, ys, 2.0f * (s2m * cs - s2n), uA);
-  rotate_unit(g, xs, ys, 2.0f * (s2m * cs + c2n), uB);
-  float rC = 1.0f;
+  const NodeEntry& Mu = tab[g.nt_off + ri * g.q_mu + qi];
+  const NodeEntry& Nu = tab[g.nt_off + nmu + rj * g.q_nu + qj];
+  const NodeEntry& Ph = tab[g.nt_off + nmu + nnu + rk * g.q_phi + qk];
+  const df sh = ld2(Mu.fs), s2m = ld2(Mu.fh2);
+  const df sn = ld2(Nu.fs), cs = ld2(Nu.fc), s2n = ld2(Nu.fh2), c2n = ld2(Nu.fg2);
+  const df sp = ld2(Ph.fs), cp = ld2(Ph.fc);
+  const df shsn = dfa::mul(sh, sn);
+  df w = dfa::mk(0.0f);
+  if (!dead) {
+    const df gw = dfa::mul(dfa::mul(ld2(Mu.fw), ld2(Nu.fw)), ld2(Ph.fw));
+    w = dfa::mul(dfa::mul(gw, shsn), dfa::add_same(dfa::mul(sh, sh), dfa::mul(sn, sn)));
+  }
+  const df rhoA = dfa::add_same(s2m, s2n), rhoB = dfa::add_same(s2m, c2n);
+  const df xs = dfa::mul(shsn, cp), ys = dfa::mul(shsn, sp);
+  const df s2mc = dfa::mul(s2m, cs);
+  df uA[3], uB[3], uC[3] = {dfa::mk(0.f), dfa::mk(0.f), dfa::mk(1.f)};
+  rotate_unit_df(g, xs, ys, dfa::scale2(dfa::sub(s2mc, s2n), 2.0f), dfa::rcp(dfa::scale2(rhoA, 2.0f)), uA);
+  rotate_unit_df(g, xs, ys, dfa::scale2(dfa::add(s2mc, c2n), 2.0f), dfa::rcp(dfa::scale2(rhoB, 2.0f)), uB);
+  df rC = dfa::mk(1.0f);
   if (g.C >= 0) {
     // offset from the third centre in the pair frame, FP64: it cancels near that centre
     const double X = g.a * Mu.s * Nu.s * Ph.c - g.xc;
     const double Yv = g.a * Mu.s * Nu.s * Ph.s;
     const double Z = g.a * Mu.c * Nu.c - g.zc;
-    rC = rotate_unit(g, (float)X, (float)Yv, (float)Z, uC);
+    const df dX = split_d(X), dY = split_d(Yv), dZ = split_d(Z);
+    rC = dfa::sqrt(dfa::add_same(dfa::add_same(dfa::mul(dX, dX), dfa::mul(dY, dY)), dfa::mul(dZ, dZ)));
+    rotate_unit_df(g, dX, dY, dZ, dfa::rcp(rC), uC);
   }
-  float* base = ops + g.op_off;
+  float* bh = ops + g.op_off;
+  float* bl = ops_lo + g.op_off;
   const int64_t ld = g.ld;
   if (g.row_W >= 0) {
-    base[(int64_t)(g.row_W + 0) * ld + p] = w;
-    base[(int64_t)(g.row_W + 1) * ld + p] = w / rhoA;
-    base[(int64_t)(g.row_W + 2) * ld + p] = w / rhoB;
-    base[(int64_t)(g.row_W + 3) * ld + p] = g.C >= 0 ? w / rC : 0.0f;
+    const df wv[4] = {w, dfa::div(w, rhoA), dfa::div(w, rhoB), g.C >= 0 ? dfa::div(w, rC) : dfa::mk(0.0f)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bh[(int64_t)(g.row_W + k) * ld + p] = wv[k].h;
+      bl[(int64_t)(g.row_W + k) * ld + p] = wv[k].l;
+    }
   }
   const float2* xi = xi_tab + g.xi_off;  // basis A, basis B, aux c0, aux c1 shells
   const int nbA = g.shb_A1 - g.shb_A0, nbB = g.shb_B1 - g.shb_B0, na0 = g.sha_1 - g.sha_0;
-  float Y[(kMaxL + 1) * (kMaxL + 1)];
+  df Y[(kMaxL + 1) * (kMaxL + 1)];
   if (g.row_F >= 0 || g.row_L >= 0) {
     for (int c = 0; c < 2; ++c) {
       const int s0 = c == 0 ? g.shb_A0 : g.shb_B0, s1 = c == 0 ? g.shb_A1 : g.shb_B1;
       if (s1 <= s0) continue;
-      const float rho = c == 0 ? rhoA : rhoB;
-      const float* u = c == 0 ? uA : uB;
-      real_ylm_u(shells_lmax_f(t.bshell, s0, s1), u[0], u[1], u[2], Y);
+      const df* u = c == 0 ? uA : uB;
+      dfa::real_ylm(shells_lmax_f(t.bshell, s0, s1), u[0], u[1], u[2], Y);
       const int roff = c == 0 ? 0 : g.nFA;
-      const float2* z = xi + (c == 0 ? 0 : nbA);
-      if (g.row_F >= 0 && g.row_L >= 0) {
-        eval_shells_x2(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_F + roff, 0, g.row_L + roff, 1);
-      } else {
-        if (g.row_F >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_F + roff, 0);
-        if (g.row_L >= 0) eval_shells_x(t.bshell, z, s0, s1, rho, Y, base, ld, p, g.row_L + roff, 1);
-      }
+      eval_shells_df(t.bshell, xi + (c == 0 ? 0 : nbA), s0, s1, c == 0 ? rhoA : rhoB, Y, bh, bl, ld, p,
+                     g.row_F >= 0 ? g.row_F + roff : -1, 0, g.row_L >= 0 ? g.row_L + roff : -1, 1, etab);
     }
   }
   if (g.row_G >= 0 || g.row_U >= 0) {
@@ -348,19 +310,14 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
       const int s0 = c == 0 ? g.sha_0 : g.sha_2, s1 = c == 0 ? g.sha_1 : g.sha_3;
       const int atom = c == 0 ? g.aux_c0 : g.aux_c1;
       if (atom < 0 || s1 <= s0) continue;
-      const float* u;
-      float rho;
+      const df* u;
+      df rho;
       if (atom == g.A) { u = uA; rho = rhoA; }
       else if (atom == g.B) { u = uB; rho = rhoB; }
       else { u = uC; rho = rC; }
-      real_ylm_u(shells_lmax_f(t.ashell, s0, s1), u[0], u[1], u[2], Y);
-      const float2* z = xi + nbA + nbB + (c == 0 ? 0 : na0);
-      if (g.row_G >= 0 && g.row_U >= 0) {
-        eval_shells_x2(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_G + roff, 0, g.row_U + roff, 2);
-      } else {
-        if (g.row_G >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_G + roff, 0);
-        if (g.row_U >= 0) eval_shells_x(t.ashell, z, s0, s1, rho, Y, base, ld, p, g.row_U + roff, 2);
-      }
+      dfa::real_ylm(shells_lmax_f(t.ashell, s0, s1), u[0], u[1], u[2], Y);
+      eval_shells_df(t.ashell, xi + nbA + nbB + (c == 0 ? 0 : na0), s0, s1, rho, Y, bh, bl, ld, p,
+                     g.row_G >= 0 ? g.row_G + roff : -1, 0, g.row_U >= 0 ? g.row_U + roff : -1, 2, etab);
       int nf = 0;
       for (int s = s0; s < s1; ++s) nf += 2 * t.ashell[s].l + 1;
       roff += nf;
@@ -372,23 +329,25 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
 
 namespace mma {
 
-constexpr int kM = 128;         // tile rows (pairs, or the bigger side of a 2-index block)
-constexpr int kTileN = 64;       // tile columns
-constexpr int kChunk = 64;      // points per scale window and smem stage (128 bytes of BF16)
-constexpr int kSlices = 4;      // 8-bit integer slices per operand value (orders 0..3 kept)
+constexpr int kM = kMmaM;
+constexpr int kTileN = kMmaN;
+constexpr int kChunk = kChunkPts;
+constexpr int kRowB = 2 * kChunkPts;            // bytes of one operand row of a stage (64)
+constexpr int kStages = 3;                      // shared-memory ring depth (chunks)
+constexpr int kChunksPerWin = kWinPts / kChunkPts;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart.
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 bytes apart.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)(16 >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset between 8-row groups
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset between 8-row groups
   d |= (uint64_t)1 << 46;             // descriptor version for sm_100 family
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  d |= (uint64_t)4 << 61;             // SWIZZLE_64B
   return d;
 }
 
@@ -428,30 +387,20 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Waits for the phase of the given parity; gives up (false) after kWaitNs nanoseconds, or
+// Waits for the phase of the given parity; gives up (false) after limit_ns nanoseconds, or
 // early once *abort (if given) is set by another role of the CTA.
 constexpr uint64_t kWaitNs = 4000000000ull;
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const int* abort = nullptr) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const int* abort = nullptr,
+                                          uint64_t limit_ns = kWaitNs) {
   if (mbar_try(mbar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(mbar, parity)) return true;
     if ((it & 255u) == 0) {
       if (abort && *(volatile const int*)abort) return false;
-      if (global_ns() - t0 > kWaitNs) return false;
+      if (global_ns() - t0 > limit_ns) return false;
     }
   }
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
@@ -483,17 +432,24 @@ __device__ __forceinline__ float pow2f(int k) {
 // image by pack_kernel; the contraction then moves it with bulk copies.  Only the 3-index
 // operand chi_i chi_j, whose rows are products of two basis rows, is formed inside the
 // contraction, from basis rows staged in shared memory.
+//
+// Slicing.  A row's values in a 128-point window are scaled by 2^(7-e) (|v| < 2^e over the
+// window) and cut into five digits v ~ s0 + s1/256 + ... + s4/256^4 of integers (each the
+// nearest integer of what the previous digits left, times 256), exact in BF16: 39 bits of the
+// window's largest value.  For a double-float value the first three digits come from the hi
+// part (exactly); the lo part (|lo| <= 2^-24 |hi|) then joins the remainder, which rounds
+// once, at 2^-17 of the fourth digit's unit; s3 can reach 256.  Accumulation bound: the
+// order-k sum sum_{i+j=k} s_i t_j over 128 points stays below 128 x 114688 < 2^24 for every
+// k <= 4, so the FP32 tensor-core accumulators hold it exactly.
 
 namespace mma {
 
-// Eight values, already scaled into (-128, 128), as four planes of 8-bit integers in BF16:
-// plane k holds the nearest integer of what planes 0..k-1 left, times 256^k.  w[k] is the
-// 16-byte group of plane k.
-__device__ __forceinline__ void slice8(const float* v, float sc, uint4* w) {
+__device__ __forceinline__ void slice8_df(const float* vh, const float* vl, float sc, uint4* w) {
   uint32_t o[kSlices][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    float r0 = v[2 * q] * sc, r1 = v[2 * q + 1] * sc;
+    float r0 = vh[2 * q] * sc, r1 = vh[2 * q + 1] * sc;
+    const float l0 = vl[2 * q] * sc * 16777216.0f, l1 = vl[2 * q + 1] * sc * 16777216.0f;
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) {
       const float a0 = rintf(r0), a1 = rintf(r1);
@@ -501,6 +457,10 @@ __device__ __forceinline__ void slice8(const float* v, float sc, uint4* w) {
       o[k][q] = *reinterpret_cast<const uint32_t*>(&p);
       r0 = (r0 - a0) * 256.0f;
       r1 = (r1 - a1) * 256.0f;
+      if (k == 2) {
+        r0 += l0;
+        r1 += l1;
+      }
     }
   }
 #pragma unroll
@@ -514,193 +474,168 @@ __device__ __forceinline__ int row_exponent(float mx) {
   return e < -110 ? kZeroExp : e;
 }
 
-// Byte offset of 16-byte group j of row r in a 128-byte-row swizzled operand tile.
-__device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)r * 128u + ((uint32_t)(j ^ (r & 7)) << 4); }
+// Byte offset of 16-byte group j (0..3) of row r in a 64-byte-row swizzled operand tile.
+__device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)r * 64u + ((uint32_t)(j ^ ((r >> 1) & 3)) << 4); }
 
 }  // namespace mma
 
-// One packing job: 64 rows of one tile of one panel, one 128-point window; eight threads per
-// row, thread (r, e) holding points [16 (e % 4), 16 (e % 4) + 16) of chunk e / 4.
-struct PackJob {
-  float v[16];
-  int pn, t, w, r, c, qq;
+// Decodes packing job `job` (panel, tile, window, 16-row group) for this thread: 8 threads per
+// row, thread qq holding points [16 qq, 16 qq + 16) of the window (chunk 4 w + qq/2, 16-byte
+// groups 2 (qq % 2) and 2 (qq % 2) + 1 of its row).
+struct PackPos {
+  int pn, t, w, r, qq;
 };
 
-// Decodes job and loads its values (source row times its weight row, zeros past K).
-__device__ __forceinline__ void pack_load(int64_t job, const DevGrid* __restrict__ grids,
-                                          const Panel* __restrict__ panels, int n_panels,
-                                          const short2* __restrict__ rows, const float* __restrict__ ops,
-                                          PackJob& J) {
+__device__ __forceinline__ PackPos pack_pos(int64_t job, const Panel* __restrict__ panels, int n_panels) {
   int lo = 0, hi = n_panels;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
     if (panels[mid].job_begin <= job) lo = mid; else hi = mid;
   }
   const Panel& pn = panels[lo];
-  const int gsh = pn.tr >> 7;  // 64-row groups per tile: 1 (tr 64) or 2 (tr 128)
+  const int G = pn.tr / kPackRows;
   const int lj = (int)(job - pn.job_begin);  // jobs of one panel < 2^31 (one launch's grid)
-  const int tw = lj >> gsh, grp = lj & gsh;
-  J.pn = lo;
-  J.t = tw / pn.nwin;
-  J.w = tw - J.t * pn.nwin;
-  J.r = 64 * grp + (threadIdx.x >> 3);
-  const int e8 = threadIdx.x & 7;
-  J.c = 2 * J.w + (e8 >> 2);
-  J.qq = e8 & 3;
-  const DevGrid& g = grids[pn.grid];
-  const int row = J.t * pn.tr + J.r;
-  const int64_t k0 = 64 * (int64_t)J.c + 16 * J.qq;
-  const float* src = nullptr;
-  const float* mul = nullptr;
-  if (row < pn.nrows && J.c < pn.nch) {
-    const short2 q = rows[pn.rows_off + row];
-    src = ops + g.op_off + (int64_t)q.x * g.ld + k0;
-    if (q.y >= 0) mul = ops + g.op_off + (int64_t)q.y * g.ld + k0;
-  }
-  const int64_t left = g.K - k0;
-  if (src && left >= 16) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    const float4* m4 = reinterpret_cast<const float4*>(mul);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float4 a = __ldg(s4 + i);
-      if (mul) {
-        const float4 bb = __ldg(m4 + i);
-        a.x *= bb.x; a.y *= bb.y; a.z *= bb.z; a.w *= bb.w;
-      }
-      J.v[4 * i] = a.x; J.v[4 * i + 1] = a.y; J.v[4 * i + 2] = a.z; J.v[4 * i + 3] = a.w;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 16; ++i) J.v[i] = (src && i < left) ? src[i] * (mul ? mul[i] : 1.0f) : 0.0f;
-  }
+  const int tw = lj / G, grp = lj - tw * G;
+  PackPos P;
+  P.pn = lo;
+  P.t = tw / pn.nwin;
+  P.w = tw - P.t * pn.nwin;
+  P.r = kPackRows * grp + (threadIdx.x >> 3);
+  P.qq = threadIdx.x & 7;
+  return P;
 }
 
-// The row's window scale (the eight threads of the row share it), its exponent, and the
-// four planes of this thread's 16 points.
-__device__ __forceinline__ void pack_store(const PackJob& J, const Panel* __restrict__ panels,
+// The row's window exponent (the eight threads of the row share it) and the five planes of
+// this thread's 16 points.
+__device__ __forceinline__ void pack_store(const PackPos& P, const Panel& pn, const float* h, const float* l,
                                            uint8_t* __restrict__ packed) {
   using namespace mma;
-  const Panel& pn = panels[J.pn];
   float mx = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fabsf(J.v[i]));
+  for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fabsf(h[i]));
   const unsigned m8 = 0xffu << ((threadIdx.x & 31) & ~7u);
   mx = fmaxf(mx, __shfl_xor_sync(m8, mx, 1));
   mx = fmaxf(mx, __shfl_xor_sync(m8, mx, 2));
   mx = fmaxf(mx, __shfl_xor_sync(m8, mx, 4));
   const int e = row_exponent(mx);
-  if ((threadIdx.x & 7) == 0)
-    *reinterpret_cast<int*>(packed + pn.exp_off + (((int64_t)J.t * pn.nwin + J.w) * pn.tr + J.r) * 4) = e;
-  const int rt = min(pn.tr, pn.nrows - J.t * pn.tr);
-  if (J.c >= pn.nch || J.r >= rt) return;
+  if (P.qq == 0)
+    *reinterpret_cast<int*>(packed + pn.exp_off + (((int64_t)P.t * pn.nwin + P.w) * pn.tr + P.r) * 4) = e;
+  const int rt = min(pn.tr, pn.nrows - P.t * pn.tr);
+  const int c = kChunksPerWin * P.w + (P.qq >> 1);
+  if (c >= pn.nch || P.r >= rt) return;
   const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
-  uint8_t* dst = packed + pn.pack_off + (int64_t)J.t * pn.nch * (4 * pn.tr * 128) + (int64_t)J.c * (4 * rt * 128);
-  const int plane = rt * 128;
+  uint8_t* dst = packed + pn.pack_off + (int64_t)P.t * pn.nch * (kSlices * pn.tr * kRowB) +
+                 (int64_t)c * (kSlices * rt * kRowB);
+  const int plane = rt * kRowB;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     uint4 wv[kSlices];
-    slice8(J.v + 8 * j, sc, wv);
+    slice8_df(h + 8 * j, l + 8 * j, sc, wv);
 #pragma unroll
-    for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(J.r, 2 * J.qq + j)) = wv[k];
+    for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(P.r, 2 * (P.qq & 1) + j)) = wv[k];
   }
 }
 
-// One CTA of 512 threads per packing job (panel, tile, 128-point window, 64-row group).
-// (Two jobs per CTA with all loads issued first measured 1-6% slower: fewer CTAs fit.)
-__global__ void __launch_bounds__(512, 3) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
+// One CTA of 128 threads per packing job.  Values: source row times its weight row
+// (double-float products), zeros past K.
+__global__ void __launch_bounds__(128) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
                                                    int n_panels, const short2* __restrict__ rows,
-                                                   const float* __restrict__ ops, uint8_t* __restrict__ packed) {
-  PackJob J;
-  pack_load(blockIdx.x, grids, panels, n_panels, rows, ops, J);
-  pack_store(J, panels, packed);
+                                                   const float* __restrict__ ops, const float* __restrict__ ops_lo,
+                                                   uint8_t* __restrict__ packed) {
+  const PackPos P = pack_pos(blockIdx.x, panels, n_panels);
+  const Panel& pn = panels[P.pn];
+  const DevGrid& g = grids[pn.grid];
+  const int row = P.t * pn.tr + P.r;
+  const int64_t k0 = (int64_t)kWinPts * P.w + 16 * P.qq;
+  int64_t src = -1, mul = -1;
+  if (row < pn.nrows) {
+    const short2 q = rows[pn.rows_off + row];
+    src = g.op_off + (int64_t)q.x * g.ld + k0;
+    if (q.y >= 0) mul = g.op_off + (int64_t)q.y * g.ld + k0;
+  }
+  const int64_t left = src >= 0 ? g.K - k0 : 0;
+  float h[16], l[16];
+#pragma unroll
+  for (int i4 = 0; i4 < 4; ++i4) {
+    float4 ah = make_float4(0.f, 0.f, 0.f, 0.f), al = ah, bh = make_float4(1.f, 1.f, 1.f, 1.f), bl = al;
+    if (left >= 4 * i4 + 4) {
+      ah = __ldg(reinterpret_cast<const float4*>(ops + src) + i4);
+      al = __ldg(reinterpret_cast<const float4*>(ops_lo + src) + i4);
+      if (mul >= 0) {
+        bh = __ldg(reinterpret_cast<const float4*>(ops + mul) + i4);
+        bl = __ldg(reinterpret_cast<const float4*>(ops_lo + mul) + i4);
+      }
+    } else if (left > 4 * i4) {
+      float* ph = &ah.x; float* pl = &al.x; float* qh = &bh.x; float* ql = &bl.x;
+      for (int i = 0; i < 4 && 4 * i4 + i < left; ++i) {
+        ph[i] = ops[src + 4 * i4 + i];
+        pl[i] = ops_lo[src + 4 * i4 + i];
+        if (mul >= 0) {
+          qh[i] = ops[mul + 4 * i4 + i];
+          ql[i] = ops_lo[mul + 4 * i4 + i];
+        }
+      }
+    }
+    const float xh[4] = {ah.x, ah.y, ah.z, ah.w}, xl[4] = {al.x, al.y, al.z, al.w};
+    const float yh[4] = {bh.x, bh.y, bh.z, bh.w}, yl[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const df v = mul >= 0 ? dfa::mul(df{xh[i], xl[i]}, df{yh[i], yl[i]}) : df{xh[i], xl[i]};
+      h[4 * i4 + i] = v.h;
+      l[4 * i4 + i] = v.l;
+    }
+  }
+  pack_store(P, pn, h, l, packed);
 }
 
 // The same packed-panel image from FP64 operand rows (row-major, stride n): used for the
 // RI 4-index product, whose operand rows are the (P|ij) columns after the forward solve.
 // Panel k's rows start at src[k]; jobs as in pack_kernel, both panels' jobs in one launch.
-// The digits are taken in FP64 (exact: the value times a power of two, rounded digit by
-// digit), each exact in BF16.
-__global__ void __launch_bounds__(512, 2) ri_pack_kernel(const Panel* __restrict__ panels, const double* __restrict__ srcA,
+// Each FP64 value is split into a double-float pair first (48 bits, beyond the 39 that the
+// digits keep).
+__global__ void __launch_bounds__(128) ri_pack_kernel(const Panel* __restrict__ panels, const double* __restrict__ srcA,
                                                       const double* __restrict__ srcB, int n, uint8_t* __restrict__ packed) {
-  using namespace mma;
-  const int64_t job = blockIdx.x;
-  const int k = panels[1].job_begin <= job ? 1 : 0;
-  const Panel& pn = panels[k];
-  const double* src = k ? srcB : srcA;
-  const int gsh = pn.tr >> 7;
-  const int lj = (int)(job - pn.job_begin);
-  const int tw = lj >> gsh, grp = lj & gsh;
-  const int t = tw / pn.nwin, w = tw - t * pn.nwin;
-  const int r = 64 * grp + (threadIdx.x >> 3), e8 = threadIdx.x & 7;
-  const int c = 2 * w + (e8 >> 2), qq = e8 & 3;
-  const int row = t * pn.tr + r;
-  const int k0 = 64 * c + 16 * qq;
-  double v[16];
+  const PackPos P = pack_pos(blockIdx.x, panels, 2);
+  const Panel& pn = panels[P.pn];
+  const double* src = P.pn ? srcB : srcA;
+  const int row = P.t * pn.tr + P.r;
+  const int k0 = kWinPts * P.w + 16 * P.qq;
+  float h[16], l[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = 0.0;
-  if (row < pn.nrows && c < pn.nch) {
-    const double* rp = src + (int64_t)row * n + k0;
-#pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (k0 + i < n) v[i] = rp[i];
+  for (int i = 0; i < 16; ++i) {
+    double v = 0.0;
+    if (row < pn.nrows && k0 + i < n) v = src[(int64_t)row * n + k0 + i];
+    h[i] = (float)v;
+    l[i] = (float)(v - (double)h[i]);
   }
-  double mx = 0.0;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) mx = fmax(mx, fabs(v[i]));
-  const unsigned m8 = 0xffu << ((threadIdx.x & 31) & ~7u);
-  mx = fmax(mx, __shfl_xor_sync(m8, mx, 1));
-  mx = fmax(mx, __shfl_xor_sync(m8, mx, 2));
-  mx = fmax(mx, __shfl_xor_sync(m8, mx, 4));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);  // mx < 2^e <= 2 mx
-  if (!(mx > 0.0) || e < -110) e = kZeroExp;
-  if (e8 == 0) *reinterpret_cast<int*>(packed + pn.exp_off + (((int64_t)t * pn.nwin + w) * pn.tr + r) * 4) = e;
-  const int rt = min(pn.tr, pn.nrows - t * pn.tr);
-  if (c >= pn.nch || r >= rt) return;
-  const double sc = e == kZeroExp ? 0.0 : ldexp(1.0, 7 - e);
-  uint8_t* dst = packed + pn.pack_off + (int64_t)t * pn.nch * (4 * pn.tr * 128) + (int64_t)c * (4 * rt * 128);
-  const int plane = rt * 128;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    uint32_t o[kSlices][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      double x0 = v[8 * j + 2 * q] * sc, x1 = v[8 * j + 2 * q + 1] * sc;
-#pragma unroll
-      for (int d = 0; d < kSlices; ++d) {
-        const double a0 = rint(x0), a1 = rint(x1);
-        const __nv_bfloat162 pr = __floats2bfloat162_rn((float)a0, (float)a1);
-        o[d][q] = *reinterpret_cast<const uint32_t*>(&pr);
-        x0 = (x0 - a0) * 256.0;
-        x1 = (x1 - a1) * 256.0;
-      }
-    }
-#pragma unroll
-    for (int d = 0; d < kSlices; ++d)
-      *reinterpret_cast<uint4*>(dst + d * plane + swz(r, 2 * qq + j)) = make_uint4(o[d][0], o[d][1], o[d][2], o[d][3]);
-  }
+  pack_store(P, pn, h, l, packed);
 }
 
 // ------------------------------------------------------------------ warp-specialised contraction
 //
-// One persistent CTA per SM, 512 threads, working through tiles (128 A rows x <= 64 B
+// One persistent CTA per SM, 512 threads, working through tiles (128 A rows x <= 48 B
 // columns x a range of 128-point windows):
-//   warp 4       loader: bulk copies of the packed A tile (and packed B tile) of every 64-point
-//                chunk into a two-stage ring, and of the staged basis rows of formed B tiles
-//                (one copy per row and window);
+//   warp 4       loader: bulk copies of the packed A tile (and packed B tile) of every 32-point
+//                chunk into a three-stage ring, and of the staged basis rows (hi and lo planes)
+//                of formed B tiles, one copy per row, plane and window;
 //   warps 0-3, 6, 7  producers: for a formed B, column c of the tile = product of two staged
-//                rows; per window they find each column's scale, then slice chunk by chunk
-//                into the B stages, so that the MMAs of one chunk overlap the slicing of the
-//                next (for a packed B they only pass each chunk on);
-//   warp 5       MMA issue: per chunk 4 K-steps x 10 slice products (orders 0..3) into the
-//                window's TMEM accumulator set (4 orders x 64 columns; two sets);
-//   warps 8-15   fold: per window, the four order sums of their TMEM lane quadrant and column
+//                rows (a double-float product); each warp owns 8 columns, four lanes per
+//                column, lane g the 16-byte group g of every chunk; per window they find each
+//                column's scale, then slice chunk by chunk into the B stages, so that the MMAs
+//                of one chunk overlap the slicing of the next (for a packed B they only pass
+//                each chunk on);
+//   warp 5       MMA issue: per chunk 2 K-steps x 5 MMAs (A plane i against B planes
+//                0..4-i, contiguous in shared memory: one MMA of N = 48 (5 - i) whose columns
+//                land on the order accumulators i..4) into the window's TMEM accumulator set
+//                (5 orders x 48 columns; two sets);
+//   warps 8-15   fold: per window, the five order sums of their TMEM lane quadrant and column
 //                half, scaled by the window's row and column exponents, into double-float
-//                registers; at the end of the tile, (hi, lo) partials to global memory.
-// All integer sums stay below 2^23 (|slice| <= 128, <= 4 products per order, 128 points), so
-// the FP32 accumulators hold them exactly.  Every wait is bounded; a timeout sets *status and
-// the CTA's abort flag, and each role leaves its loops at its next wait.
+//                registers (orders 0, 1 and 2 join the sum exactly through TwoSums, orders 3-4
+//                as one FP32 term); at the end of the tile, (hi, lo) partials to global memory.
+// Every wait is bounded (wait_ns in the main loops, the fixed kWaitNs for the drains); a
+// timeout sets *status and the CTA's abort flag, and each role leaves its loops at its next
+// wait; the loader then waits for its copies in flight and the MMA lane for its MMAs before
+// the TMEM is released.
 
 namespace ws {
 
@@ -709,12 +644,13 @@ constexpr int kLoadWarp = 4, kMmaWarp = 5, kFoldWarp0 = 8;
 constexpr int kRawStride = 132;  // floats per staged row: 128 points + 4 (bank spread)
 
 struct Smem {
-  alignas(1024) uint8_t a[2][mma::kSlices][mma::kM * 128];
-  alignas(1024) uint8_t b[2][mma::kSlices][mma::kTileN * 128];
-  alignas(16) float raw[2][kPairTileRows][kRawStride];
+  alignas(1024) uint8_t a[mma::kStages][kSlices][mma::kM * mma::kRowB];
+  alignas(1024) uint8_t b[mma::kStages][kSlices][mma::kTileN * mma::kRowB];
+  alignas(16) float raw[2][2][kPairTileRows][kRawStride];  // [buffer][hi, lo][row][point]
   int eb[2][mma::kTileN];
   float sbw[8][mma::kTileN];  // fold warp k: the column scales of the current window
-  alignas(8) uint64_t a_full[2], b_ready[2], stage_free[2], tmem_full[2], tmem_free[2], raw_full[2], raw_free[2];
+  alignas(8) uint64_t a_full[mma::kStages], b_ready[mma::kStages], stage_free[mma::kStages];
+  uint64_t tmem_full[2], tmem_free[2], raw_full[2], raw_free[2];
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
@@ -745,16 +681,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
-__device__ __forceinline__ bool wait(uint64_t* b, uint32_t parity, const int* abort = nullptr) {
-  return mma::mbar_wait(mma::smem_u32(b), parity, abort);
+__device__ __forceinline__ bool wait(uint64_t* b, uint32_t parity, const int* abort, uint64_t limit_ns) {
+  return mma::mbar_wait(mma::smem_u32(b), parity, abort, limit_ns);
 }
+
+// Ring position of chunk c: stage c % kStages, completed rounds c / kStages.
+__device__ __forceinline__ int stage_of(uint32_t c) { return (int)(c % mma::kStages); }
+__device__ __forceinline__ uint32_t round_of(uint32_t c) { return c / mma::kStages; }
 
 // What every role needs to know about an item.
 struct Geo {
   const MmaBlock* blk;
   int64_t K;
   int nch, nwin, w0, w1;
-  int nt, ntp;      // B columns of the tile and their multiple of 16
+  int nt;  // B columns of the tile
   bool formed;
   const PairTile* pt;
 };
@@ -765,16 +705,17 @@ __device__ __forceinline__ Geo geo(const GemmItem& it, const MmaBlock* blocks, c
   q.blk = blocks + it.block;
   const MmaBlock& b = *q.blk;
   q.K = grids[b.grid].K;
-  q.nch = (int)((q.K + 63) / 64);
-  q.nwin = (q.nch + 1) / 2;
+  q.nch = (int)((q.K + mma::kChunk - 1) / mma::kChunk);
+  q.nwin = (q.nch + mma::kChunksPerWin - 1) / mma::kChunksPerWin;
   q.w0 = it.chunk * b.win_per;
   q.w1 = min(q.nwin, q.w0 + b.win_per);
   q.formed = b.b_panel < 0;
   q.pt = q.formed ? ptiles + b.ptile_off + it.tn : nullptr;
   q.nt = q.formed ? q.pt->ncols : min(mma::kTileN, b.n - it.tn * mma::kTileN);
-  q.ntp = (q.nt + 15) & ~15;
   return q;
 }
+
+__device__ __forceinline__ int chunks_in(const Geo& q, int win) { return min(mma::kChunksPerWin, q.nch - mma::kChunksPerWin * win); }
 
 __device__ __forceinline__ void fail(Smem& sm, int* status, int code) {
   *(volatile int*)&sm.abort = 1;
@@ -788,9 +729,10 @@ __device__ __forceinline__ bool aborted(Smem& sm) { return *(volatile int*)&sm.a
 __global__ void __launch_bounds__(ws::kThreads, 1)
     contract_ws_kernel(const DevGrid* __restrict__ grids, const MmaBlock* __restrict__ blocks,
                        const GemmItem* __restrict__ items, const int* __restrict__ cta_begin,
-                       const Panel* __restrict__ panels,
-                       const PairTile* __restrict__ ptiles, const float* __restrict__ ops,
-                       const uint8_t* __restrict__ packed, float2* __restrict__ part, int* __restrict__ status) {
+                       const Panel* __restrict__ panels, const PairTile* __restrict__ ptiles,
+                       const float* __restrict__ ops, const float* __restrict__ ops_lo,
+                       const uint8_t* __restrict__ packed, float2* __restrict__ part, int* __restrict__ status,
+                       uint64_t wait_ns) {
   using namespace mma;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   ws::Smem& sm = *reinterpret_cast<ws::Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -801,10 +743,12 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < kStages; ++s) {
       ws::mbar_init(&sm.a_full[s], 1);
       ws::mbar_init(&sm.b_ready[s], 6);
       ws::mbar_init(&sm.stage_free[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
       ws::mbar_init(&sm.tmem_full[s], 1);
       ws::mbar_init(&sm.tmem_free[s], 8);
       ws::mbar_init(&sm.raw_full[s], 1);
@@ -833,61 +777,62 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       const Panel& pa = panels[b.a_panel];
       const Panel* pb = q.formed ? nullptr : panels + b.b_panel;
       for (int win = q.w0; win < q.w1 && run; ++win, ++w) {
-        const int nck = min(2, q.nch - 2 * win);
+        const int nck = ws::chunks_in(q, win);
         if (q.formed) {
           const int rb = rw & 1;
-          const bool ok = rw < 2 || ws::wait(&sm.raw_free[rb], ((rw - 2) >> 1) & 1, &sm.abort);
+          const bool ok = rw < 2 || ws::wait(&sm.raw_free[rb], ((rw - 2) >> 1) & 1, &sm.abort, wait_ns);
           run = __all_sync(kFull, ok && !ws::aborted(sm));
           if (!run) { ws::fail(sm, status, 4); break; }
-          const int nr = q.pt->nrows;
-          if (lane == 0) ws::mbar_expect_tx(&sm.raw_full[rb], (uint32_t)nr * 512u);
+          const int nr = q.pt->nrows;  // <= kPairTileRows (16): lanes 0-15 hi, 16-31 lo
+          if (lane == 0) ws::mbar_expect_tx(&sm.raw_full[rb], (uint32_t)nr * 2u * 512u);
           __syncwarp();
-          if (lane < nr)
-            ws::bulk_g2s(sm.raw[rb][lane], ops + g.op_off + (int64_t)q.pt->rows[lane] * g.ld + 128 * (int64_t)win,
+          const int rr = lane & 15, pl = lane >> 4;
+          if (rr < nr)
+            ws::bulk_g2s(sm.raw[rb][pl][rr],
+                         (pl ? ops_lo : ops) + g.op_off + (int64_t)q.pt->rows[rr] * g.ld + (int64_t)kWinPts * win,
                          512u, &sm.raw_full[rb]);
           last_raw = (int)rw;
           ++rw;
         }
         for (int j = 0; j < nck; ++j, ++c) {
-          const int s = c & 1, ch = 2 * win + j;
-          const bool ok = c < 2 || ws::wait(&sm.stage_free[s], ((c - 2) >> 1) & 1, &sm.abort);
+          const int s = ws::stage_of(c), ch = kChunksPerWin * win + j;
+          const bool ok = c < (uint32_t)kStages ||
+                          ws::wait(&sm.stage_free[s], (ws::round_of(c) - 1) & 1, &sm.abort, wait_ns);
           run = __all_sync(kFull, ok && !ws::aborted(sm));
           if (!run) { ws::fail(sm, status, 4); break; }
-          // the stored rows of the tiles, one bulk copy per plane (lanes 0-3: A, 4-7: B)
+          // the stored rows of the tiles, one bulk copy per plane (lanes 0-4: A, 5-9: B)
           const int ra = min(kM, pa.nrows - it.tm * kM);
           const int rbw = pb ? min(kTileN, pb->nrows - it.tn * kTileN) : 0;
-          if (lane == 0) ws::mbar_expect_tx(&sm.a_full[s], 4u * 128u * (uint32_t)(ra + rbw));
+          if (lane == 0) ws::mbar_expect_tx(&sm.a_full[s], (uint32_t)(kSlices * kRowB * (ra + rbw)));
           __syncwarp();
-          if (lane < 4) {
-            const uint8_t* src = packed + pa.pack_off + (int64_t)it.tm * pa.nch * (4 * kM * 128) +
-                                 (int64_t)ch * (4 * ra * 128) + (int64_t)lane * ra * 128;
-            ws::bulk_g2s(sm.a[s][lane], src, 128u * (uint32_t)ra, &sm.a_full[s]);
-          } else if (lane < 8 && pb) {
-            const int k = lane - 4;
-            const uint8_t* src = packed + pb->pack_off + (int64_t)it.tn * pb->nch * (4 * kTileN * 128) +
-                                 (int64_t)ch * (4 * rbw * 128) + (int64_t)k * rbw * 128;
-            ws::bulk_g2s(sm.b[s][k], src, 128u * (uint32_t)rbw, &sm.a_full[s]);
+          if (lane < kSlices) {
+            const uint8_t* src = packed + pa.pack_off + (int64_t)it.tm * pa.nch * (kSlices * kM * kRowB) +
+                                 (int64_t)ch * (kSlices * ra * kRowB) + (int64_t)lane * ra * kRowB;
+            ws::bulk_g2s(sm.a[s][lane], src, (uint32_t)(kRowB * ra), &sm.a_full[s]);
+          } else if (lane < 2 * kSlices && pb) {
+            const int k = lane - kSlices;
+            const uint8_t* src = packed + pb->pack_off + (int64_t)it.tn * pb->nch * (kSlices * kTileN * kRowB) +
+                                 (int64_t)ch * (kSlices * rbw * kRowB) + (int64_t)k * rbw * kRowB;
+            ws::bulk_g2s(sm.b[s][k], src, (uint32_t)(kRowB * rbw), &sm.a_full[s]);
           }
           __syncwarp();
           last_a = (int)c;
         }
       }
     }
-    // drain: nothing may still be copying into shared memory when the CTA exits
-    if (!run) {
-      for (int k = last_a; k >= 0 && k > last_a - 2; --k) ws::wait(&sm.a_full[k & 1], (k >> 1) & 1);
-      for (int k = last_raw; k >= 0 && k > last_raw - 2; --k) ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1);
-    }
+    // drain: nothing may still be copying into shared memory when the CTA exits (another
+    // role may have given up after this loop ended; the phases waited for here are the last
+    // ones issued on each barrier, complete at once when the copies were consumed)
+    for (int k = last_a; k >= 0 && k > last_a - kStages; --k)
+      ws::wait(&sm.a_full[ws::stage_of(k)], ws::round_of(k) & 1, nullptr, kWaitNs);
+    for (int k = last_raw; k >= 0 && k > last_raw - 2; --k)
+      ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1, nullptr, kWaitNs);
   } else if (warp < 4 || warp == 6 || warp == 7) {
     // ------------------------------------------------------------------ producers
-    // Six warps.  A window's 64 columns are 16 rounds of 4 columns; producer warp pw takes
-    // rounds pw, pw + 6, pw + 12.  In a round, eight lanes share a column, lane g owning
-    // points 8g..8g+7 of both chunks: they read contiguous 32-byte pieces of the column's two
-    // rows (one row per quarter warp), find the column's window maximum by shuffles, and
-    // write the eight 16-byte groups of the column's 128-byte row in each plane.
-    const int pw = warp < 4 ? warp : warp - 2;
-    const int g = lane & 7;
-    const unsigned col_mask = 0xffu << (lane & 24);
+    const int pw = warp < 4 ? warp : warp - 2;  // 0..5
+    const int col = 8 * pw + (lane >> 2);       // 0..47: this lane's column of the tile
+    const int g = lane & 3;                     // 16-byte group of each chunk's row
+    const unsigned col_mask = 0xfu << (lane & 28);
     bool run = true;  // warp-uniform
     for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
@@ -895,95 +840,89 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       if (!q.formed) {
         // packed B: the loader brings it; b_ready still completes one phase per chunk
         for (int win = q.w0; win < q.w1 && run; ++win, ++w) {
-          const int nck = min(2, q.nch - 2 * win);
+          const int nck = ws::chunks_in(q, win);
           for (int j = 0; j < nck; ++j, ++c) {
-            const bool ok = c < 2 || ws::wait(&sm.stage_free[c & 1], ((c - 2) >> 1) & 1, &sm.abort);
+            const int s = ws::stage_of(c);
+            const bool ok = c < (uint32_t)kStages ||
+                            ws::wait(&sm.stage_free[s], (ws::round_of(c) - 1) & 1, &sm.abort, wait_ns);
             run = __all_sync(kFull, ok && !ws::aborted(sm));
             if (!run) { ws::fail(sm, status, 5); break; }
-            if (lane == 0) ws::mbar_arrive(&sm.b_ready[c & 1]);
+            if (lane == 0) ws::mbar_arrive(&sm.b_ready[s]);
           }
         }
         continue;
       }
-      // this lane's columns (one per round) and their two rows
-      int colr[3], dxr[3], dyr[3];
-      bool validr[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const int R = pw + 6 * r;
-        colr[r] = 4 * R + (lane >> 3);
-        validr[r] = R < 16 && colr[r] < q.nt;
-        dxr[r] = validr[r] ? q.pt->dx[colr[r]] : 0;
-        dyr[r] = validr[r] ? q.pt->dy[colr[r]] : 0;
-      }
+      const bool valid = col < q.nt;
+      const int dx = valid ? q.pt->dx[col] : 0, dy = valid ? q.pt->dy[col] : 0;
       for (int win = q.w0; win < q.w1 && run; ++win, ++w, ++rw) {
-        const int nck = min(2, q.nch - 2 * win);
+        const int nck = ws::chunks_in(q, win);
         const int rb = rw & 1, set = w & 1;
-        bool ok = ws::wait(&sm.raw_full[rb], (rw >> 1) & 1, &sm.abort);
-        if (ok && w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort);
+        bool ok = ws::wait(&sm.raw_full[rb], (rw >> 1) & 1, &sm.abort, wait_ns);
+        if (ok && w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort, wait_ns);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 5); break; }
-        const int64_t wleft = q.K - 128 * (int64_t)win;  // points of the window that exist
-        float v[3][2][8];
-        float sc[3], mxr[3];
+        const int64_t wleft = q.K - (int64_t)kWinPts * win;  // points of the window that exist
+        float vh[kChunksPerWin][8], vl[kChunksPerWin][8];
+        float mx = 0.0f;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          float mx = 0.0f;
+        for (int cc = 0; cc < kChunksPerWin; ++cc) {
+          const int p0 = kChunk * cc + 8 * g;
+          const float* xh = sm.raw[rb][0][dx] + p0;
+          const float* xl = sm.raw[rb][1][dx] + p0;
+          const float* yh = sm.raw[rb][0][dy] + p0;
+          const float* yl = sm.raw[rb][1][dy] + p0;
+          const int64_t left = valid ? wleft - p0 : 0;
+          if (left >= 8) {
+            float a[8], al[8], bb[8], bl[8];
+            *reinterpret_cast<float4*>(a) = *reinterpret_cast<const float4*>(xh);
+            *reinterpret_cast<float4*>(a + 4) = *reinterpret_cast<const float4*>(xh + 4);
+            *reinterpret_cast<float4*>(al) = *reinterpret_cast<const float4*>(xl);
+            *reinterpret_cast<float4*>(al + 4) = *reinterpret_cast<const float4*>(xl + 4);
+            *reinterpret_cast<float4*>(bb) = *reinterpret_cast<const float4*>(yh);
+            *reinterpret_cast<float4*>(bb + 4) = *reinterpret_cast<const float4*>(yh + 4);
+            *reinterpret_cast<float4*>(bl) = *reinterpret_cast<const float4*>(yl);
+            *reinterpret_cast<float4*>(bl + 4) = *reinterpret_cast<const float4*>(yl + 4);
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            const int p0 = 64 * j + 8 * g;
-            const float* rx = sm.raw[rb][dxr[r]] + p0;
-            const float* ry = sm.raw[rb][dyr[r]] + p0;
-            const int64_t left = validr[r] ? wleft - p0 : 0;
-            if (left >= 8) {
-              const float4 a0 = *reinterpret_cast<const float4*>(rx);
-              const float4 a1 = *reinterpret_cast<const float4*>(rx + 4);
-              const float4 b0 = *reinterpret_cast<const float4*>(ry);
-              const float4 b1 = *reinterpret_cast<const float4*>(ry + 4);
-              v[r][j][0] = a0.x * b0.x; v[r][j][1] = a0.y * b0.y; v[r][j][2] = a0.z * b0.z; v[r][j][3] = a0.w * b0.w;
-              v[r][j][4] = a1.x * b1.x; v[r][j][5] = a1.y * b1.y; v[r][j][6] = a1.z * b1.z; v[r][j][7] = a1.w * b1.w;
-            } else {
-#pragma unroll
-              for (int i = 0; i < 8; ++i) v[r][j][i] = i < left ? rx[i] * ry[i] : 0.0f;
+            for (int i = 0; i < 8; ++i) {
+              const df v = dfa::mul(df{a[i], al[i]}, df{bb[i], bl[i]});
+              vh[cc][i] = v.h;
+              vl[cc][i] = v.l;
             }
+          } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(v[r][j][i]));
+            for (int i = 0; i < 8; ++i) {
+              df v = dfa::mk(0.0f);
+              if (i < left) v = dfa::mul(df{xh[i], xl[i]}, df{yh[i], yl[i]});
+              vh[cc][i] = v.h;
+              vl[cc][i] = v.l;
+            }
           }
-          mxr[r] = mx;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(vh[cc][i]));
         }
-        // the column maxima over the eight lanes of each column, the three rounds interleaved
+        // the column's window maximum over its four lanes
+        mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 1));
+        mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 2));
+        const int e = row_exponent(mx);
+        if (g == 0) sm.eb[set][col] = e;
+        const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
 #pragma unroll
-        for (int d = 1; d < 8; d <<= 1)
-#pragma unroll
-          for (int r = 0; r < 3; ++r) mxr[r] = fmaxf(mxr[r], __shfl_xor_sync(col_mask, mxr[r], d));
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int e = row_exponent(mxr[r]);
-          if (g == 0 && pw + 6 * r < 16) sm.eb[set][colr[r]] = e;
-          sc[r] = e == kZeroExp ? 0.0f : pow2f(7 - e);
-        }
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          if (j < nck && run) {
-            const bool okc = c < 2 || ws::wait(&sm.stage_free[c & 1], ((c - 2) >> 1) & 1, &sm.abort);
+        for (int cc = 0; cc < kChunksPerWin; ++cc) {
+          if (cc < nck && run) {
+            const int s = ws::stage_of(c);
+            const bool okc = c < (uint32_t)kStages ||
+                             ws::wait(&sm.stage_free[s], (ws::round_of(c) - 1) & 1, &sm.abort, wait_ns);
             run = __all_sync(kFull, okc && !ws::aborted(sm));
             if (!run) {
               ws::fail(sm, status, 5);
             } else {
-              uint8_t* dst = sm.b[c & 1][0];
+              uint4 wv[kSlices];
+              slice8_df(vh[cc], vl[cc], sc, wv);
 #pragma unroll
-              for (int r = 0; r < 3; ++r) {
-                if (pw + 6 * r < 16) {
-                  uint4 wv[kSlices];
-                  slice8(v[r][j], sc[r], wv);
-#pragma unroll
-                  for (int k = 0; k < kSlices; ++k)
-                    *reinterpret_cast<uint4*>(dst + k * (kTileN * 128) + swz(colr[r], g)) = wv[k];
-                }
-              }
+              for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(sm.b[s][k] + swz(col, g)) = wv[k];
               fence_async_smem();
               __syncwarp();
-              if (lane == 0) ws::mbar_arrive(&sm.b_ready[c & 1]);
+              if (lane == 0) ws::mbar_arrive(&sm.b_ready[s]);
               ++c;
             }
           }
@@ -1001,19 +940,20 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
         bool ok = true;
         for (int win = q.w0; win < q.w1 && ok; ++win, ++w) {
-          const int nck = min(2, q.nch - 2 * win);
+          const int nck = ws::chunks_in(q, win);
           const int set = w & 1;
-          if (w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort);
+          if (w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort, wait_ns);
           const uint32_t tset = tmem + (uint32_t)set * 256u;
           for (int j = 0; j < nck && ok; ++j, ++c) {
-            const int s = c & 1;
-            ok = ws::wait(&sm.a_full[s], (c >> 1) & 1, &sm.abort);
-            if (ok) ok = ws::wait(&sm.b_ready[s], (c >> 1) & 1, &sm.abort);
+            const int s = ws::stage_of(c);
+            const uint32_t par = ws::round_of(c) & 1;
+            ok = ws::wait(&sm.a_full[s], par, &sm.abort, wait_ns);
+            if (ok) ok = ws::wait(&sm.b_ready[s], par, &sm.abort, wait_ns);
             if (!ok) break;
             fence_after();
-            // The B planes of a stage are contiguous (64 rows each), so plane i of A against
-            // planes 0..3-i of B is one MMA of N = 64 (4 - i) whose columns land on the order
-            // accumulators i..3 (order k at TMEM columns 64k..64k+63 of the set).
+            // The B planes of a stage are contiguous (48 rows each), so plane i of A against
+            // planes 0..4-i of B is one MMA of N = 48 (5 - i) whose columns land on the order
+            // accumulators i..4 (order k at TMEM columns 48k..48k+47 of the set).
 #pragma unroll
             for (int k = 0; k < kChunk / 16; ++k) {
               const uint32_t ko = 32u * k;
@@ -1021,7 +961,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
               for (int i = 0; i < kSlices; ++i) {
                 const uint64_t da = make_desc(smem_u32(sm.a[s][i]) + ko);
-                mma_bf16(tset + 64u * i, da, db, make_idesc(64 * (kSlices - i)), (j > 0 || k > 0 || i > 0) ? 1u : 0u);
+                mma_bf16(tset + (uint32_t)(kTileN * i), da, db, make_idesc(kTileN * (kSlices - i)),
+                         (j > 0 || k > 0 || i > 0) ? 1u : 0u);
               }
             }
             mma_commit(smem_u32(&sm.stage_free[s]));
@@ -1031,19 +972,19 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         }
         if (!ok) break;
       }
-      // drain: every issued MMA must be complete before the TMEM is released
-      if (ws::aborted(sm)) {
-        mma_commit(smem_u32(&sm.drain));
-        ws::wait(&sm.drain, 0);
-      }
+      // drain: every issued MMA must be complete before the TMEM is released (also when
+      // another role gave up after this loop ended)
+      mma_commit(smem_u32(&sm.drain));
+      ws::wait(&sm.drain, 0, nullptr, kWaitNs);
     }
     __syncwarp();
   } else if (warp >= ws::kFoldWarp0) {
     // ------------------------------------------------------------------ fold
     const int ew = warp - ws::kFoldWarp0;  // 0..7
     const int quad = warp & 3;             // TMEM lane quadrant this warp may access
-    const int half = ew >> 2;              // 16-column groups gq with gq % 2 == half
+    const int half = ew >> 2;              // columns [24 half, 24 half + 24)
     const int row_in_tile = quad * 32 + lane;
+    const int my_col = 24 * half + lane;   // lanes 0-23: the column whose scale this lane loads
     bool run = true;  // warp-uniform
     for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
@@ -1052,15 +993,15 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       const Panel& pa = panels[b.a_panel];
       const Panel* pb = q.formed ? nullptr : panels + b.b_panel;
       const int rows_valid = min(kM, b.m - it.tm * kM);  // real rows of the A tile
-      float H[32], L[32];
+      float H[24], L[24];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) { H[j] = 0.0f; L[j] = 0.0f; }
-      // the window's exponents (A rows from the packed panel, B columns from the packed panel,
-      // one per lane for this warp's 32 columns, or from the producers), loaded one window ahead
-      const int my_col = (2 * (lane >> 4) + half) * 16 + (lane & 15);
+      for (int j = 0; j < 24; ++j) { H[j] = 0.0f; L[j] = 0.0f; }
+      // the window's exponents (A rows from the packed panel; B columns from the packed panel,
+      // one per lane for this warp's 24 columns, or from the producers), loaded one window ahead
       const int* ea_src = reinterpret_cast<const int*>(packed + pa.exp_off) + (int64_t)it.tm * pa.nwin * kM + row_in_tile;
-      const int* eb_src = pb ? reinterpret_cast<const int*>(packed + pb->exp_off) + (int64_t)it.tn * pb->nwin * kTileN + my_col
-                             : nullptr;
+      const int* eb_src = (pb && lane < 24)
+                              ? reinterpret_cast<const int*>(packed + pb->exp_off) + (int64_t)it.tn * pb->nwin * kTileN + my_col
+                              : nullptr;
       int ea_next = __ldg(ea_src + (int64_t)q.w0 * kM);
       int eb_next = eb_src ? __ldg(eb_src + (int64_t)q.w0 * kTileN) : 0;
       for (int win = q.w0; win < q.w1; ++win, ++w) {
@@ -1070,43 +1011,40 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
           ea_next = __ldg(ea_src + (int64_t)(win + 1) * kM);
           if (eb_src) eb_next = __ldg(eb_src + (int64_t)(win + 1) * kTileN);
         }
-        const bool ok = ws::wait(&sm.tmem_full[set], (w >> 1) & 1, &sm.abort);
+        const bool ok = ws::wait(&sm.tmem_full[set], (w >> 1) & 1, &sm.abort, wait_ns);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 7); break; }
         fence_after();
         // column scales 2^(e_b - 7) for this warp, row scale 2^(e_a - 7) for this thread
         float* sbw = sm.sbw[ew];
-        sbw[my_col] = pow2f((pb ? eb_lane : sm.eb[set][my_col]) - 7);
+        if (lane < 24) sbw[my_col] = pow2f((pb ? eb_lane : sm.eb[set][my_col]) - 7);
         const float sa = pow2f(ea - 7);
         __syncwarp();
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * 256u;
+        // a warp whose 32 rows are all past the tile's last real row has nothing to fold
+        if (quad * 32 < rows_valid) {
 #pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-          const int gq = 2 * gi + half;  // 16-column group
-          // a warp whose 32 rows are all past the tile's last real row has nothing to fold
-          if (gq * 16 < q.ntp && quad * 32 < rows_valid) {
+          for (int gi = 0; gi < 3; ++gi) {
+            const int c0 = 24 * half + 8 * gi;  // first of 8 columns
+            if (c0 < q.nt) {
+              float o[kSlices][8];
 #pragma unroll
-            for (int sub = 0; sub < 2; ++sub) {
-              const int c0 = gq * 16 + 8 * sub;  // first of 8 columns
-              float o0[8], o1[8], o2[8], o3[8];
-              tmem_ld8(lane_base + 0 * kTileN + c0, o0);
-              tmem_ld8(lane_base + 1 * kTileN + c0, o1);
-              tmem_ld8(lane_base + 2 * kTileN + c0, o2);
-              tmem_ld8(lane_base + 3 * kTileN + c0, o3);
+              for (int k = 0; k < kSlices; ++k) tmem_ld8(lane_base + (uint32_t)(kTileN * k + c0), o[k]);
               tmem_wait_ld();
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                const int qq = gi * 16 + 8 * sub + j;
+                const int qq = 8 * gi + j;
                 const float sc = sa * sbw[c0 + j];  // 2^(e_a + e_b - 14)
-                // order 0 (exact integers) into the double-float sum, orders 1..3 (each 256
-                // times smaller) as one FP32 correction
-                const float x = o0[j] * sc;
-                const float t = H[qq] + x;
-                const float bb = t - H[qq];
-                const float err = (H[qq] - (t - bb)) + (x - bb);
-                H[qq] = t;
-                const float lo = fmaf(o3[j], 5.9604644775390625e-8f, fmaf(o2[j], 1.52587890625e-5f, o1[j] * 0.00390625f));
-                L[qq] += fmaf(lo, sc, err);
+                // orders 0, 1, 2 (exact integers times powers of two) into the double-float sum
+                // through TwoSums, orders 3 and 4 as one FP32 term
+                const df s0 = dfa::two_sum(H[qq], o[0][j] * sc);
+                const df s1 = dfa::two_sum(s0.h, o[1][j] * (sc * 0.00390625f));
+                const df s2 = dfa::two_sum(s1.h, o[2][j] * (sc * 1.52587890625e-5f));
+                const float tail = fmaf(o[4][j], 2.3283064365386963e-10f, o[3][j] * 5.9604644775390625e-8f) * sc;
+                const float lo = L[qq] + ((s0.l + s1.l) + (s2.l + tail));
+                const df r = dfa::fast_two_sum(s2.h, lo);
+                H[qq] = r.h;
+                L[qq] = r.l;
               }
             }
           }
@@ -1121,15 +1059,11 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       if (grow < b.m) {
         float2* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n + (int64_t)grow * b.n;
 #pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-          const int gq = 2 * gi + half;
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int cc = gq * 16 + j;
-            if (cc < q.nt) {
-              const int col = q.formed ? q.pt->col[cc] : it.tn * kTileN + cc;
-              out[col] = make_float2(H[gi * 16 + j], L[gi * 16 + j]);
-            }
+        for (int j = 0; j < 24; ++j) {
+          const int cc = 24 * half + j;
+          if (cc < q.nt) {
+            const int ocol = q.formed ? q.pt->col[cc] : it.tn * kTileN + cc;
+            out[ocol] = make_float2(H[j], L[j]);
           }
         }
       }
@@ -1148,12 +1082,12 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 // order (consecutive threads read consecutive partials).
 __global__ void __launch_bounds__(256) reduce_mixed_kernel(const DevGrid* __restrict__ grids,
                                                            const MmaBlock* __restrict__ blocks, int n_blocks,
-                                                           const int64_t* __restrict__ elem_begin, int64_t n_elems,
-                                                           const short2* __restrict__ rows,
+                                                           const int64_t* __restrict__ elem_begin, int64_t e0,
+                                                           int64_t e1, const short2* __restrict__ rows,
                                                            const double* __restrict__ rowc,
                                                            const float2* __restrict__ part, double* __restrict__ res) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_elems) return;
+  const int64_t idx = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= e1) return;
   int lo = 0, hi = n_blocks;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -1176,7 +1110,26 @@ __global__ void __launch_bounds__(256) reduce_mixed_kernel(const DevGrid* __rest
   res[b.res_off + e] = s * ca * cb;
 }
 
+// Diagnostics: operand rows (hi + lo) times their FP64 row constants, as FP64 rows of K values.
+__global__ void combine_rows_kernel(const float* __restrict__ h, const float* __restrict__ l,
+                                    const double* __restrict__ rc, int nrows, int64_t K, int64_t ld,
+                                    double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)nrows * K) return;
+  const int r = (int)(i / K);
+  const int64_t p = i - (int64_t)r * K;
+  out[i] = ((double)h[r * ld + p] + (double)l[r * ld + p]) * rc[r];
+}
+
 // ------------------------------------------------------------------ launchers
+
+cudaError_t launch_combine_rows(const float* h, const float* l, const double* rc, int nrows, int64_t K, int64_t ld,
+                                double* out, cudaStream_t s) {
+  const int64_t n = (int64_t)nrows * K;
+  if (n == 0) return cudaSuccess;
+  combine_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h, l, rc, nrows, K, ld, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, const double* edges, NodeEntry* tab,
                          cudaStream_t s) {
@@ -1187,9 +1140,9 @@ cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, con
 }
 
 cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const float2* xi, float* ops,
-                              cudaStream_t s) {
+                              float* ops_lo, cudaStream_t s) {
   if (t.n_pblocks == 0) return cudaSuccess;
-  eval_mixed_kernel<<<t.n_pblocks, 128, 0, s>>>(t, tab, xi, ops);
+  eval_mixed_kernel<<<t.n_pblocks, 128, 0, s>>>(t, tab, xi, ops, ops_lo);
   return cudaGetLastError();
 }
 
@@ -1200,33 +1153,34 @@ cudaError_t prepare_kernels() {
 }
 
 cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
-                        const float* ops, uint8_t* packed, cudaStream_t s) {
+                        const float* ops, const float* ops_lo, uint8_t* packed, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
-  pack_kernel<<<(unsigned)n_jobs, 512, 0, s>>>(grids, panels, n_panels, rows, ops, packed);
+  pack_kernel<<<(unsigned)n_jobs, 128, 0, s>>>(grids, panels, n_panels, rows, ops, ops_lo, packed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items,
                                const int* cta_begin, int n_ctas, const Panel* panels, const PairTile* ptiles,
-                               const float* ops, const uint8_t* packed, float2* part, int* status, cudaStream_t s) {
+                               const float* ops, const float* ops_lo, const uint8_t* packed, float2* part, int* status,
+                               uint64_t wait_ns, cudaStream_t s) {
   if (n_ctas == 0) return cudaSuccess;
   contract_ws_kernel<<<n_ctas, ws::kThreads, ws_smem_bytes(), s>>>(grids, blocks, items, cta_begin, panels, ptiles, ops,
-                                                                   packed, part, status);
+                                                                   ops_lo, packed, part, status, wait_ns);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ri_pack(const Panel* panels, int64_t n_jobs, const double* srcA, const double* srcB, int n,
                            uint8_t* packed, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
-  ri_pack_kernel<<<(unsigned)n_jobs, 512, 0, s>>>(panels, srcA, srcB, n, packed);
+  ri_pack_kernel<<<(unsigned)n_jobs, 128, 0, s>>>(panels, srcA, srcB, n, packed);
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
-                                int64_t n_elems, const short2* rows, const double* rowc, const float2* part,
+                                int64_t e0, int64_t e1, const short2* rows, const double* rowc, const float2* part,
                                 double* res, cudaStream_t s) {
-  if (n_elems == 0) return cudaSuccess;
-  reduce_mixed_kernel<<<(unsigned)((n_elems + 255) / 256), 256, 0, s>>>(grids, blocks, n_blocks, elem_begin, n_elems,
+  if (e1 <= e0) return cudaSuccess;
+  reduce_mixed_kernel<<<(unsigned)((e1 - e0 + 255) / 256), 256, 0, s>>>(grids, blocks, n_blocks, elem_begin, e0, e1,
                                                                          rows, rowc, part, res);
   return cudaGetLastError();
 }

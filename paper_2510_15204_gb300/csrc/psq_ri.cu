@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) eri_kernel(int n, int64_t m, const double
 //
 // (ij|kl) = sum_R B[R][ij] B[R][kl] is the contraction of eq 9 with the aux index R in the
 // place of the points: the pair columns of B become operand rows (transposed into Bt), are
-// packed as in the mixed path (four 8-bit slices per value under a power-of-two scale per
+// packed as in the mixed path (five 8-bit slices per value under a power-of-two scale per
 // row and 128 aux functions), and the tcgen05 contraction and its FP64 range reduction run
 // unchanged on them (one block, A = the c pairs, B = the d pairs, all row constants 1).
 
@@ -240,10 +240,10 @@ struct RiMixedLayout {
 RiMixedLayout ri_mixed_layout(int n, int64_t nc, int64_t nd, int sm_count) {
   RiMixedLayout L{};
   L.n = n; L.nc = nc; L.nd = nd;
-  L.nch = (n + 63) / 64;
-  L.nwin = (L.nch + 1) / 2;
-  L.tmA = (int)((nc + 127) / 128);
-  L.tnB = (int)((nd + 63) / 64);
+  L.nch = (n + kChunkPts - 1) / kChunkPts;
+  L.nwin = (n + kWinPts - 1) / kWinPts;
+  L.tmA = (int)((nc + kMmaM - 1) / kMmaM);
+  L.tnB = (int)((nd + kMmaN - 1) / kMmaN);
   const int64_t tiles = (int64_t)L.tmA * L.tnB;
   const int64_t want = 2LL * sm_count;  // at least two items per SM: ranges of aux windows
   int r = tiles >= want ? 1 : (int)std::min<int64_t>(L.nwin, (want + tiles - 1) / tiles);
@@ -251,8 +251,8 @@ RiMixedLayout ri_mixed_layout(int n, int64_t nc, int64_t nd, int sm_count) {
   L.n_ranges = (L.nwin + L.win_per - 1) / L.win_per;
   L.n_items = tiles * L.n_ranges;
   L.n_ctas = (int)std::min<int64_t>(L.n_items, sm_count);
-  L.jobsA = (int64_t)L.tmA * L.nwin * 2;
-  L.jobsB = (int64_t)L.tnB * L.nwin;
+  L.jobsA = (int64_t)L.tmA * L.nwin * (kMmaM / kPackRows);
+  L.jobsB = (int64_t)L.tnB * L.nwin * (kMmaN / kPackRows);
   size_t o = 0;
   auto sec = [&](size_t bytes) { const size_t at = o; o = up(o + bytes); return at; };
   L.o_status = sec(sizeof(int));
@@ -267,10 +267,10 @@ RiMixedLayout ri_mixed_layout(int n, int64_t nc, int64_t nd, int sm_count) {
   L.o_bt = sec(sizeof(double) * (size_t)(nc + nd) * n);
   size_t pk = 0;
   auto psec = [&](size_t bytes) { const size_t at = pk; pk = up(pk + bytes); return (int64_t)at; };
-  L.packA = psec((size_t)nc * L.nch * 4 * 128);
-  L.expA = psec((size_t)L.tmA * L.nwin * 128 * 4);
-  L.packB = psec((size_t)nd * L.nch * 4 * 128);
-  L.expB = psec((size_t)L.tnB * L.nwin * 64 * 4);
+  L.packA = psec((size_t)nc * L.nch * kSlices * 2 * kChunkPts);
+  L.expA = psec((size_t)L.tmA * L.nwin * kMmaM * 4);
+  L.packB = psec((size_t)nd * L.nch * kSlices * 2 * kChunkPts);
+  L.expB = psec((size_t)L.tnB * L.nwin * kMmaN * 4);
   L.o_pack = sec(pk);
   L.o_part = sec(sizeof(float2) * (size_t)L.n_ranges * nc * nd);
   L.total = o;
@@ -287,9 +287,9 @@ __global__ void ri_setup_kernel(RiMixedLayout L, char* __restrict__ ws) {
     g->K = L.n;
     g->rc_off = 0;
     Panel* pn = reinterpret_cast<Panel*>(ws + L.o_pn);
-    pn[0].grid = 0; pn[0].rows_off = 0; pn[0].nrows = (int)L.nc; pn[0].tr = 128; pn[0].n_tiles = L.tmA;
+    pn[0].grid = 0; pn[0].rows_off = 0; pn[0].nrows = (int)L.nc; pn[0].tr = kMmaM; pn[0].n_tiles = L.tmA;
     pn[0].nch = L.nch; pn[0].nwin = L.nwin; pn[0].pack_off = L.packA; pn[0].exp_off = L.expA; pn[0].job_begin = 0;
-    pn[1].grid = 0; pn[1].rows_off = (int)L.nc; pn[1].nrows = (int)L.nd; pn[1].tr = 64; pn[1].n_tiles = L.tnB;
+    pn[1].grid = 0; pn[1].rows_off = (int)L.nc; pn[1].nrows = (int)L.nd; pn[1].tr = kMmaN; pn[1].n_tiles = L.tnB;
     pn[1].nch = L.nch; pn[1].nwin = L.nwin; pn[1].pack_off = L.packB; pn[1].exp_off = L.expB; pn[1].job_begin = L.jobsA;
     MmaBlock* b = reinterpret_cast<MmaBlock*>(ws + L.o_blk);
     b->grid = 0; b->m = (int)L.nc; b->n = (int)L.nd; b->a_off = 0; b->b_off = (int)L.nc;
@@ -443,10 +443,11 @@ extern "C" psq_status psq_ri_eri_mixed(int n, int64_t m, const double* d_B, int6
   if (launch_ri_pack(pn, L.jobsA + L.jobsB, btA, btB, n, packed, s) != cudaSuccess) return launched();
   if (launch_contract_ws((const DevGrid*)(ws + L.o_grid), (const MmaBlock*)(ws + L.o_blk),
                          (const GemmItem*)(ws + L.o_items), (const int*)(ws + L.o_cb), L.n_ctas, pn, nullptr, nullptr,
-                         packed, (float2*)(ws + L.o_part), (int*)(ws + L.o_status), s) != cudaSuccess)
+                         nullptr, packed, (float2*)(ws + L.o_part), (int*)(ws + L.o_status), 4000000000ull,
+                         s) != cudaSuccess)
     return launched();
   if (launch_reduce_mixed((const DevGrid*)(ws + L.o_grid), (const MmaBlock*)(ws + L.o_blk), 1,
-                          (const int64_t*)(ws + L.o_eb), nc * nd, (const short2*)(ws + L.o_rows),
+                          (const int64_t*)(ws + L.o_eb), 0, nc * nd, (const short2*)(ws + L.o_rows),
                           (const double*)(ws + L.o_rowc), (const float2*)(ws + L.o_part), d_out, s) != cudaSuccess)
     return launched();
   return launched();

@@ -17,22 +17,32 @@ void* g_addr[kMaxDevices] = {};
 
 }  // namespace
 
-extern "C" psq_status psq_compute_noalloc(psq_job* job, unsigned mask, double* d_out[5], void* stream) {
+psq_status psq::noalloc_scratch(void** ptr) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return psq::set_error(PSQ_ERR_CUDA, cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return psq::set_error(PSQ_ERR_UNSUPPORTED, "device index out of range");
-  void* ptr = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      e = cudaGetSymbolAddress(&g_addr[dev], g_scratch);
-      if (e != cudaSuccess) {
-        g_addr[dev] = nullptr;
-        return psq::set_error(PSQ_ERR_CUDA, cudaGetErrorString(e));
-      }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    e = cudaGetSymbolAddress(&g_addr[dev], g_scratch);
+    if (e != cudaSuccess) {
+      g_addr[dev] = nullptr;
+      return psq::set_error(PSQ_ERR_CUDA, cudaGetErrorString(e));
     }
-    ptr = g_addr[dev];
   }
+  *ptr = g_addr[dev];
+  return PSQ_OK;
+}
+
+extern "C" psq_status psq_compute_noalloc(psq_job* job, unsigned mask, double* d_out[5], void* stream) {
+  if (!job) return psq::set_error(PSQ_ERR_ARG, "job is NULL");
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return psq::set_error(PSQ_ERR_CUDA, cudaGetErrorString(e));
+  // the scratch address is per device: the job's device must be the current one
+  if (dev != psq::job_device(job)) return psq::set_error(PSQ_ERR_ARG, "the current device is not the job's device");
+  void* ptr = nullptr;
+  const psq_status st = psq::noalloc_scratch(&ptr);
+  if (st != PSQ_OK) return st;
   return psq::compute_on(job, mask, ptr, PSQ_NOALLOC_SCRATCH_BYTES, d_out, stream, true);
 }

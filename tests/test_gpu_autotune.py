@@ -37,10 +37,10 @@ def test_autotune_keeps_results_and_plan(precision):
     assert J.workspace_bytes(mask) <= ws.numel()
     after = _run(J, mask, ws, out)
     # another split sums the same points in other ranges: FP64 partials agree to rounding;
-    # the mixed path's double-float range sums carry FP32 corrections (~1e-10 relative)
+    # the mixed path's double-float window folds agree to its error (1e-9 absolute)
     tol = 1e-12 if precision == 0 else 1e-9
     for k in before:
-        scale = np.abs(before[k]).max()
+        scale = np.abs(before[k]).max() if precision == 0 else 1.0  # mixed: absolute
         np.testing.assert_allclose(after[k], before[k], rtol=0, atol=tol * scale, err_msg=k)
     # a graph captured after tuning replays the tuned plan
     stream = torch.cuda.Stream()

@@ -2,9 +2,8 @@
 36 pair grids with N_mu 15..30 and N_nu 10..20, 252 refined grids, 55.8 M points): every
 class on the GPU, compared with the oracle on sampled blocks it can compute one by one
 (one-, two- and three-centre S/T/V, (P|Q) and (P|ij) blocks, C-C, C-H and H-H).
-FP64 path: 1e-12 of each element's absolute-term sum C.  Mixed path: 2e-6 of
-max(C, 1e-4 x the class's largest C); its function values are FP32, so elements far below the
-class scale carry FP32-level absolute, not relative, error."""
+FP64 path: 1e-12 of each element's absolute-term sum C.  Mixed path: 1e-9 absolute (its
+target), relative errors printed."""
 import numpy as np
 import pytest
 
@@ -33,7 +32,7 @@ def _fn_slices(shells, nat):
     return out
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
 def test_c3h6_sampled_blocks(ref, precision, tol):
     import torch
     import paper_2510_15204_gb300 as P
@@ -51,15 +50,13 @@ def test_c3h6_sampled_blocks(ref, precision, tol):
     torch.cuda.empty_cache()
     bs = _fn_slices(job.basis, job.n_atoms)
     ax = _fn_slices(job.aux, job.n_atoms)
-    worst = {}
-
-    floor = 0.0 if precision == 0 else 1e-4  # mixed: errors are measured against 1e-4 of the class scale
+    worst, absw = {}, {}
 
     def check(k, idx):
         scale = np.maximum(np.abs(R[k][idx]), R["abs" + k][idx])
-        scale = np.maximum(scale, floor * R["abs" + k].max())
-        e = np.abs(got[k][idx] - R[k][idx]) / np.where(scale > 0, scale, 1.0)
-        worst[k] = max(worst.get(k, 0.0), float(e.max()))
+        d = np.abs(got[k][idx] - R[k][idx])
+        worst[k] = max(worst.get(k, 0.0), float((d / np.where(scale > 0, scale, 1.0)).max()))
+        absw[k] = max(absw.get(k, 0.0), float(d.max()))
 
     for (A, B) in PAIRS:
         for k in ("S", "T", "V"):
@@ -68,6 +65,8 @@ def test_c3h6_sampled_blocks(ref, precision, tol):
         check("J2", (ax[C], ax[D]))
     for (C, A, B) in TRIPLES:
         check("J3", (ax[C], bs[A], bs[B]))
-    print("\nc3h6 precision %d worst rel-to-C:" % precision, {k: "%.2e" % v for k, v in worst.items()})
-    for k, v in worst.items():
-        assert v < tol, (k, v)
+    print("\nc3h6 precision %d worst rel / abs:" % precision,
+          {k: "%.2e / %.2e" % (worst[k], absw[k]) for k in worst})
+    for k in worst:
+        # FP64: relative to C; mixed: absolute
+        assert (worst[k] if precision == 0 else absw[k]) <= tol, (k, worst[k], absw[k])

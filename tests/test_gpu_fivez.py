@@ -1,7 +1,7 @@
 """The pentuple-zeta stress workload at full size: triatomic of Z in {6,7,8}, 5s4p3d2f1g basis
 (55 per atom), 8s7p6d5f4g3h aux (163 per atom), grids 30/25/16 with Q = (5,4,4) (960,000 points
 per pair grid, refined grids more).  GPU vs oracle on sampled blocks the oracle computes one
-by one: FP64 path to 1e-12 of C, mixed path to 2e-6 of max(C, 1e-4 x the class's largest C)."""
+by one: FP64 path to 1e-12 of C, mixed path to 1e-9 absolute (its target)."""
 import numpy as np
 import pytest
 
@@ -30,7 +30,7 @@ def _fn_slices(shells, nat):
     return out
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-6)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
 def test_fivez_sampled_blocks(ref, precision, tol):
     import torch
     import paper_2510_15204_gb300 as P
@@ -47,12 +47,10 @@ def test_fivez_sampled_blocks(ref, precision, tol):
     del ws
     torch.cuda.empty_cache()
     bs, ax = _fn_slices(job.basis, job.n_atoms), _fn_slices(job.aux, job.n_atoms)
-    floor = 0.0 if precision == 0 else 1e-4
     worst, absw = {}, {}
 
     def check(k, idx):
         scale = np.maximum(np.abs(R[k][idx]), R["abs" + k][idx])
-        scale = np.maximum(scale, floor * R["abs" + k].max())
         d = np.abs(got[k][idx] - R[k][idx])
         worst[k] = max(worst.get(k, 0.0), float((d / np.where(scale > 0, scale, 1.0)).max()))
         absw[k] = max(absw.get(k, 0.0), float(d.max()))
@@ -66,5 +64,6 @@ def test_fivez_sampled_blocks(ref, precision, tol):
         check("J3", (ax[C], bs[A], bs[B]))
     print("\nfivez precision %d worst rel / abs:" % precision,
           {k: "%.2e / %.2e" % (worst[k], absw[k]) for k in worst})
-    for k, v in worst.items():
-        assert v < tol, (k, v)
+    for k in worst:
+        # FP64: relative to C; mixed: absolute
+        assert (worst[k] if precision == 0 else absw[k]) <= tol, (k, worst[k], absw[k])

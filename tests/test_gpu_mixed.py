@@ -1,12 +1,10 @@
-"""Parity of the mixed-precision CUDA path (FP32 function values, tcgen05 contraction of
-exact 8-bit integer slices with FP32 accumulation, double-float and FP64 sums) with the
-FP64 CPU oracle.
+"""Parity of the mixed-precision CUDA path (double-float function values and weights, tcgen05
+contraction of five exact 8-bit integer slices with FP32 accumulation, double-float and FP64
+sums) with the FP64 CPU oracle.
 
-Reported per class: the largest absolute error and the largest error relative to
-max(C, 1e-4 x the class's largest C), C = the element's absolute-term sum (function values are
-FP32, so elements far below the class scale carry FP32-level absolute error).  Bars: the
-relative bar MIXED_REL holds for every class; the absolute errors are printed (the target
-for them is 1e-9, which FP32 function values do not reach).
+The bar is the mixed path's target: every element of every class within MIXED_ABS = 1e-9
+absolute of the oracle.  Reported per class: the largest absolute error and the largest
+error relative to max(|value|, C), C = the element's absolute-term sum.
 """
 import numpy as np
 import pytest
@@ -17,7 +15,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 CLASSES = ("S", "T", "V", "J2", "J3")
-MIXED_REL = 2e-6
+MIXED_ABS = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -46,14 +44,13 @@ def run(P, ctx, job, mask, precision):
 
 
 def errors(got, ref, mask):
-    """(largest absolute error, largest error relative to max(C, 1e-4 x the class's largest C))."""
+    """(largest absolute error, largest error relative to max(|value|, C)) per class."""
     rep = {}
     for i, k in enumerate(CLASSES):
         if not (mask >> i) & 1:
             continue
         d = np.abs(got[k] - ref[k])
         scale = np.maximum(np.abs(ref[k]), ref["abs" + k])
-        scale = np.maximum(scale, 1e-4 * ref["abs" + k].max())
         rel = d / np.where(scale > 0, scale, 1.0)
         rep[k] = (float(d.max()), float(rel.max()))
     return rep
@@ -68,13 +65,12 @@ def test_mixed_matches_oracle(P, ctx, make):
     rep = errors(got, ref, mask)
     print("\n%s mixed errors (abs, rel-to-C):" % job.name, {k: "%.2e %.2e" % v for k, v in rep.items()})
     for k, (ab, rel) in rep.items():
-        assert rel < MIXED_REL, (k, ab, rel)
+        assert ab <= MIXED_ABS, (k, ab, rel)
 
 
 def test_mixed_small_blocks_and_ragged_tail(P, ctx):
-    """Grids whose point counts are not multiples of the 64-point chunk, N_SP = 1, Q = 4
-    (cell-aligned chunks; chunks that straddle coarse cells are covered below), blocks
-    narrower than one MMA tile."""
+    """Grids whose point counts are not multiples of the 32-point chunk or the 128-point
+    window, N_SP = 1, Q = 4, blocks narrower than one MMA tile."""
     job = synth.triatomic_oh2(3)
     job.specs = [(7, 5, 3, 4, 4, 4, 1)]
     mask = oracle.ALL
@@ -83,11 +79,11 @@ def test_mixed_small_blocks_and_ragged_tail(P, ctx):
     rep = errors(got, ref, mask)
     print("\nragged mixed errors:", {k: "%.2e %.2e" % v for k, v in rep.items()})
     for k, (ab, rel) in rep.items():
-        assert rel < MIXED_REL, (k, ab, rel)
+        assert ab <= MIXED_ABS, (k, ab, rel)
 
 
 def test_mixed_wide_blocks(P, ctx):
-    """More than 128 pair rows and more than 64 aux columns: several M and N tiles."""
+    """More than 128 pair rows and more than 48 aux columns: several M and N tiles."""
     job = synth.fivez_diatomic(0)
     job.specs = [(8, 6, 4, 4, 4, 4, 2)]
     mask = oracle.J3 | oracle.J2 | oracle.S
@@ -96,7 +92,7 @@ def test_mixed_wide_blocks(P, ctx):
     rep = errors(got, ref, mask)
     print("\nwide mixed errors:", {k: "%.2e %.2e" % v for k, v in rep.items()})
     for k, (ab, rel) in rep.items():
-        assert rel < MIXED_REL, (k, ab, rel)
+        assert ab <= MIXED_ABS, (k, ab, rel)
 
 
 def test_mixed_agrees_with_fp64_path(P, ctx):
@@ -105,14 +101,13 @@ def test_mixed_agrees_with_fp64_path(P, ctx):
     a = run(P, ctx, job, oracle.ALL, P.FP64)
     b = run(P, ctx, job, oracle.ALL, P.MIXED)
     for k in CLASSES:
-        scale = max(1.0, float(np.abs(a[k]).max()))
-        assert np.abs(a[k] - b[k]).max() < 1e-5 * scale, k
+        assert np.abs(a[k] - b[k]).max() <= MIXED_ABS, k
 
 
 def test_mixed_chunks_straddling_coarse_cells(P, ctx):
-    """Q = (3,5,3): 45-point cells, so 64-point scale chunks straddle cells of very different
-    magnitude on this deliberately coarse grid.  Known weak spot: the kinetic class reaches
-    ~3e-5 of C here (1e-7 on the production grids); bar 1e-4."""
+    """Q = (3,5,3): 45-point cells, so 128-point scale windows straddle cells of very different
+    magnitude on this deliberately coarse grid (each value keeps 39 bits of its window's
+    largest, so the relative error of small elements grows; the absolute bar holds)."""
     job = synth.triatomic_oh2(3)
     job.specs = [(7, 5, 3, 3, 5, 3, 1)]
     mask = oracle.ALL
@@ -121,4 +116,4 @@ def test_mixed_chunks_straddling_coarse_cells(P, ctx):
     rep = errors(got, ref, mask)
     print("\nstraddling mixed errors:", {k: "%.2e %.2e" % v for k, v in rep.items()})
     for k, (ab, rel) in rep.items():
-        assert rel < 1e-4, (k, ab, rel)
+        assert ab <= MIXED_ABS, (k, ab, rel)

@@ -2,7 +2,10 @@
 application whose memory manager owns the GPU, a loop that must not pay cudaMalloc's
 synchronisation): it runs on the library's own fixed device scratch array.  Its results must
 match psq_compute's on a caller-allocated workspace, on two calls in a row (the scratch keeps
-the previous call's contents).  This file is collected last on purpose."""
+the previous call's contents), for the FP64 path and then for the mixed path on the same
+scratch (node tables, packed operands and the status word left over from other calls); after
+each call psq_check reads the status word through the scratch.  This file is collected last
+on purpose."""
 import numpy as np
 import pytest
 
@@ -39,11 +42,33 @@ def test_noalloc_matches_compute_twice():
     for call in range(2):
         out = {k: torch.full_like(v, float("nan")) for k, v in ref_out.items()}
         J.compute_noalloc(mask, out)
+        J.check(mask, None)  # the status word in the scratch
         torch.cuda.synchronize()
         for k in out:
             got = out[k].cpu().numpy()
             assert np.isfinite(got).all(), (call, k)
             assert _rel(got, ref[k], absref["abs" + k]) <= TOL, (call, k)
+
+
+def test_noalloc_mixed_on_reused_scratch():
+    """The mixed path after the FP64 calls on the same scratch, twice: bit for bit the results of
+    psq_compute on a fresh workspace (same plan, same arithmetic)."""
+    import torch
+    import paper_2510_15204_gb300 as P
+    ctx = P.Context(0)
+    J = P.Job.from_synth(ctx, synth.h2_fp64(1), P.MIXED)
+    mask = oracle.ALL
+    assert J.workspace_bytes(mask) <= 64 << 20
+    ws, ref_out = J.alloc(mask)
+    J.compute(mask, ws, ref_out)
+    J.check(mask, ws)
+    ref = {k: v.cpu().numpy() for k, v in ref_out.items()}
+    for call in range(2):
+        out = {k: torch.full_like(v, float("nan")) for k, v in ref_out.items()}
+        J.compute_noalloc(mask, out)
+        J.check(mask, None)
+        for k in out:
+            assert np.array_equal(out[k].cpu().numpy(), ref[k]), (call, k)
 
 
 def test_noalloc_rejects_unplanned_and_oversized():
