@@ -7,11 +7,16 @@ resident in device memory.  Metric: useful point-basis^2 contractions per second
 contraction = one w f g multiply-accumulate into one matrix element; the count follows the
 assembly rule: every matrix element integrated once on one grid).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload triatomic_oh2]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3h6]
                     [--precision fp64|mixed] [--impl psq|reference]
 
-Prints ONE JSON line on rank 0.  ``--impl reference`` times the CPU oracle (the paper's
-method written plainly in numpy FP64) on the host cores instead.
+The default workload is the propanediyl-shaped C3H6 job (9 atoms, 228 basis / 693 aux
+functions, 36 pair + 252 refined grids, 55.8 M points), the largest single-GPU configuration.
+Prints ONE JSON line on rank 0, with the mixed path's largest absolute error per class
+against the FP64 oracle on sampled blocks (and against the plain FP64 GPU path on every
+element), the plain FP64 path's throughput on the same job, and a short serving run.
+``--impl reference`` times the CPU oracle (the paper's method written plainly in numpy FP64)
+on the host cores instead.
 """
 from __future__ import annotations
 
@@ -38,15 +43,17 @@ FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is pro
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400, help="timed steps (default: ~0.5 s of the default workload)")
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: a few seconds of the workload)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="psq", choices=["psq", "reference"])
-    ap.add_argument("--workload", default="triatomic_oh2")
+    ap.add_argument("--workload", default="c3h6")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--fp64-steps", type=int, default=3, help="steps of the plain FP64 path timed beside")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="steps of the plain FP64 path timed beside")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the per-class errors against the oracle")
+    ap.add_argument("--no-serve-block", action="store_true", help="skip the short serving run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default work split")
     ap.add_argument("--no-ri", action="store_true", help="skip timing the RI 4-index assembly")
@@ -78,21 +85,34 @@ def aggregate(times_s, units_per_rank, world, device="cuda"):
 # ------------------------------------------------------------------------------ CPU oracle
 
 def oracle_sample(job):
-    """A bounded sample of the workload for the CPU oracle: the sub-molecule of atoms 0 and 1
-    (their basis and aux shells, the same grid spec and classes), i.e. one pair grid."""
+    """The reference arm's step: a bounded sample of the workload for the CPU oracle, the
+    sub-molecule of atoms 0 and 1 (their basis and aux shells, their pair's grid spec, every
+    class), i.e. one pair grid."""
     import synth
-    keep = (0, 1)
-    basis = [s for s in job.basis if s[0] in keep]
-    aux = [s for s in job.aux if s[0] in keep]
-    spec = job.spec_for_pair(0, 1)
-    sub = synth.Job(job.name + "_pair01", job.atoms[:2], basis, aux, [spec], job.mask)
+    sub = synth.sub_molecule(job, (0, 1))
+    spec = sub.specs[0]
     return sub, "atoms 0-1 of %s (one %dx%dx%d Q%d%d%d pair grid, %s classes)" % (
         job.name, spec[0], spec[1], spec[2], spec[3], spec[4], spec[5], "all" if job.mask == 31 else job.mask)
 
 
+def baseline_sample(job):
+    """The cpu_baseline sample: a three-atom sub-molecule of the workload (atoms 0, 1 and the
+    last atom: for C3H6 two carbons and a hydrogen) with every class, i.e. three pair grids and
+    three grids refined around the third centre, 3-centre V and (P|ij) included; the whole job
+    when it has at most three atoms."""
+    import synth
+    if job.n_atoms <= 3:
+        return job, "%s in full (%d grids, every class)" % (job.name, job.n_atoms * (job.n_atoms - 1) // 2 * (
+            1 + (job.n_atoms - 2)))
+    keep = (0, 1, job.n_atoms - 1)
+    sub = synth.sub_molecule(job, keep)
+    return sub, "atoms %d, %d, %d of %s (3 pair + 3 refined grids with its grid specs, every class)" % (
+        keep + (job.name,))
+
+
 def time_oracle(job, min_seconds=10.0, max_runs=20):
     import oracle
-    sub, desc = oracle_sample(job)
+    sub, desc = baseline_sample(job)
     work = oracle.contractions(sub, sub.mask)
     runs, t0 = 0, time.perf_counter()
     while True:
@@ -106,7 +126,64 @@ def time_oracle(job, min_seconds=10.0, max_runs=20):
             "sample": "%s, %d run(s), %.1f s, numpy FP64 (BLAS threads = all cores)" % (desc, runs, el)}
 
 
+def accuracy_blocks(job):
+    """Blocks of the workload the oracle computes one by one for the error report: S, T, V of
+    a heavy-heavy and a light-light pair (one-, two- and three-centre V contributions), (P|Q)
+    of atoms 0-1, (P|ij) of the last atom's aux on the pair 0-1 grid refined around it."""
+    n = job.n_atoms
+    pairs = [(0, 1)] + ([(n - 2, n - 1)] if n > 3 else [])
+    aux_pairs = [(0, 1)]
+    triples = [(n - 1, 0, 1)] if n >= 3 else [(1, 0, 1)]
+    return pairs, aux_pairs, triples
+
+
+def accuracy(job, got):
+    """Largest absolute error per class of `got` (host arrays) against the oracle on the
+    sampled blocks, and the oracle's seconds."""
+    import numpy as np
+    import oracle
+    pairs, aux_pairs, triples = accuracy_blocks(job)
+    t0 = time.perf_counter()
+    R = oracle.compute(job, mask=job.mask, with_abs=False, j3_triples=triples, pairs=pairs, aux_pairs=aux_pairs)
+    el = time.perf_counter() - t0
+
+    def sl(shells, X):
+        off = sum(2 * s[2] + 1 for s in shells if s[0] < X)
+        return slice(off, off + sum(2 * s[2] + 1 for s in shells if s[0] == X))
+
+    err = {}
+    for k in ("S", "T", "V"):
+        if k in got:
+            err[k] = max(float(np.abs(got[k][sl(job.basis, A), sl(job.basis, B)] -
+                                       R[k][sl(job.basis, A), sl(job.basis, B)]).max()) for A, B in pairs)
+    if "J2" in got:
+        err["J2"] = max(float(np.abs(got["J2"][sl(job.aux, C), sl(job.aux, D)] -
+                                      R["J2"][sl(job.aux, C), sl(job.aux, D)]).max()) for C, D in aux_pairs)
+    if "J3" in got:
+        err["J3"] = max(float(np.abs(got["J3"][sl(job.aux, C), sl(job.basis, A), sl(job.basis, B)] -
+                                      R["J3"][sl(job.aux, C), sl(job.basis, A), sl(job.basis, B)]).max())
+                        for C, A, B in triples)
+    desc = "oracle blocks: S/T/V %s, J2 %s, J3 (aux atom, i atom, j atom) %s" % (pairs, aux_pairs, triples)
+    return err, desc, el
+
+
+def line_config(job, args, world=1):
+    """The `config` of both arms' lines (the same dict: workload, sizes, precision, L2 note)."""
+    return {"workload": args.workload, "seed": args.seed, "precision": args.precision, "n_bf": job.n_bf,
+            "n_aux": job.n_aux, "classes": "S,T,V,J2,J3" if job.mask == 31 else job.mask,
+            "l2": "working set above the 129 MB L2 (no flush needed)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def default_steps(args):
+    if args.steps is not None:
+        return args.steps
+    return {"triatomic_oh2": 400, "h2_fp64": 400}.get(args.workload, 10)
+
+
 def reference_arm(args):
+    """The CPU oracle, as it stands, on the host cores: each step is the oracle_sample of the
+    workload (atoms 0-1, one pair grid, every class)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
@@ -115,20 +192,21 @@ def reference_arm(args):
     job = synth.WORKLOADS[args.workload](args.seed)
     sub, desc = oracle_sample(job)
     work = oracle.contractions(sub, sub.mask)
+    steps = default_steps(args)
     for _ in range(args.warmup):
         oracle.compute(sub, mask=sub.mask, with_abs=False)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         oracle.compute(sub, mask=sub.mask, with_abs=False)
     el = time.perf_counter() - t0
-    value = work * args.steps / el
+    value = work * steps / el
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "seed": args.seed, "sample": desc},
+        "config": line_config(job, args),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -284,6 +362,65 @@ def recorded_traffic(kernel, workload, precision):
 
 # ------------------------------------------------------------------------------ serving
 
+def serve_block(P, ctx, args, rate=20.0, n_jobs=60, n_fp64=3):
+    """A short serving run for the bench line: a Poisson stream of random molecules (2..9
+    atoms, DZ/TZ/QZ-sized bases, config-2 grids) through the continuous-batching server on the
+    mixed path, and the stream's first jobs as per-job plain FP64 launches (FIFO)."""
+    import threading
+    import numpy as np
+    import torch
+    import synth
+    mask = P.ALL
+    stream = synth.serving_stream(seed=args.seed, rate=rate, n_jobs=n_jobs)
+    jobs = [P.Job.from_synth(ctx, j, P.MIXED) for _, j in stream]
+    outs = [{k: torch.empty(sh, dtype=torch.float64).pin_memory() for k, sh in J.out_shapes(mask).items()}
+            for J in jobs]
+    for J in jobs:
+        J.workspace_bytes(mask)  # plan up front: planning is host work, not serving latency
+    work = sum(J.stats(mask)["contractions"] for J in jobs)
+    server = P.Server(ctx, arena_bytes=int(torch.cuda.mem_get_info()[0] * 0.5), max_inflight=6)
+    tickets = [None] * len(jobs)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for i, (t_arr, _) in enumerate(stream):
+            d = t0 + t_arr - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[i] = server.submit(jobs[i], mask, outs[i])
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    lat = [server.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    server.close()
+    res = {"rate_per_s": rate, "jobs": len(jobs), "p50_s": float(np.percentile(lat, 50)),
+           "p99_s": float(np.percentile(lat, 99)), "jobs_per_s": len(jobs) / wall,
+           "contractions_per_s": work / wall, "precision": "mixed (1e-9 absolute)"}
+    lat64, busy, t_gpu = [], 0.0, 0.0
+    stream64 = stream[:n_fp64]
+    work64 = 0.0
+    for (t_arr, j) in stream64:
+        J = P.Job.from_synth(ctx, j, P.FP64)
+        work64 += J.stats(mask)["contractions"]
+        ws, out = J.alloc(mask)
+        host = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in out.items()}
+        t1 = time.perf_counter()
+        J.compute_host(mask, ws, out, host)
+        dt = time.perf_counter() - t1
+        t_gpu += dt
+        start = max(t_arr, busy)
+        busy = start + dt
+        lat64.append(busy - t_arr)
+        del ws, out
+        torch.cuda.empty_cache()
+    res["fp64_per_job"] = {"jobs": len(stream64), "p50_s": float(np.percentile(lat64, 50)),
+                           "p99_s": float(np.percentile(lat64, 99)), "contractions_per_s": work64 / t_gpu,
+                           "note": "the stream's first jobs, one launch sequence per job, FIFO"}
+    return res
+
+
 def serve_main(args):
     """Poisson stream of random molecules (2..9 atoms, Z in {1,6,7,8}, DZ/TZ/QZ-sized bases,
     config-2 grids) through the continuous-batching server (mixed precision), against the
@@ -426,6 +563,7 @@ def main():
 
     job = synth.WORKLOADS[args.workload](args.seed)
     mask = job.mask
+    args.steps = default_steps(args)
     ctx = P.Context(local)
     prec = P.MIXED if args.precision == "mixed" else P.FP64
     J = P.Job.from_synth(ctx, job, prec)
@@ -479,6 +617,7 @@ def main():
 
     # the plain FP64 path on the same job ("vs plain FP64"), a few steps
     plain = None
+    host_mixed = {k: v.cpu().numpy() for k, v in out.items()}
     if prec == P.MIXED and args.fp64_steps > 0:
         J64 = P.Job.from_synth(ctx, job, P.FP64)
         ws64, out64 = J64.alloc(mask)
@@ -492,10 +631,19 @@ def main():
             f1.record(stream)
             torch.cuda.synchronize()
         fms = f0.elapsed_time(f1) / args.fp64_steps
+        # every element of the mixed result against the plain FP64 GPU path (itself within 1e-12
+        # of the oracle's absolute-term sums in the tests)
+        dev = {k: float((out64[k].cpu() - torch.from_numpy(host_mixed[k])).abs().max()) for k in out}
         plain = {"value": st["contractions"] / (fms / 1e3), "ms_per_step": fms, "steps": args.fp64_steps,
-                 "speedup_of_mixed": fms / (ms / args.steps)}
+                 "speedup_of_mixed": fms / (ms / args.steps), "workspace_gb": J64.workspace_bytes(mask) / 1e9,
+                 "max_abs_dev_of_mixed_every_element": dev}
         del ws64, out64, J64
         torch.cuda.empty_cache()
+    acc = None
+    if prec == P.MIXED and not args.no_accuracy and rank == 0:
+        err, desc, osec = accuracy(job, host_mixed)
+        acc = {"max_abs_err_vs_oracle": err, "target": 1e-9, "met": all(v <= 1e-9 for v in err.values()),
+               "blocks": desc, "oracle_s": osec}
 
     # end to end through the C ABI with host buffers (tables up, matrices down, every step)
     host = {k: torch.empty(v.shape, dtype=torch.float64).pin_memory() for k, v in out.items()}
@@ -517,22 +665,27 @@ def main():
     # roofline of the dominant kernel, timed live inside the timed region
     kind = max(prof, key=lambda k: prof[k][0])
     kms, kcount = prof[kind]
-    per_launch_s = kms / kcount / 1e3
+    # (per launch: the summed time of the kind over the step's launches, i.e. per step)
+    per_launch_s = kms / args.steps / 1e3
     if kind == "contract":
         flops = 2.0 * st["contractions"]
         if prec == P.FP64:
             roof = {"bound": "alu", "achieved": flops / per_launch_s / 1e12, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
         else:
-            # the tensor pipe's roofline counts the MMAs it issues: 10 slice products per useful tile
+            # achieved counts the method's work (2 FLOPs per useful contraction); the tensor pipe
+            # issues 15 slice products per useful product on padded 128 x 48 tiles
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-            roof = {"bound": "tensor", "achieved": st["issued_flops"] / per_launch_s / 1e12,
+            issued = st["issued_flops"] / per_launch_s / 1e12
+            roof = {"bound": "tensor", "achieved": flops / per_launch_s / 1e12,
                     "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "peak_source": "measured bf16 burst",
-                    "counts": "issued bf16 MMA FLOPs (8-bit slice products, padded tiles)",
-                    "useful_tflops": flops / per_launch_s / 1e12}
+                    "counts": "useful FLOPs (2 per contraction)",
+                    "issued_tflops": issued, "issued_frac": issued / peaks["bf16_tflops"],
+                    "issued_counts": "bf16 MMA FLOPs issued: 15 slice products of 128 x 48 x 32 per item and chunk"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
     roof["kernel"] = kind
+    roof["launches_per_step"] = kcount / args.steps
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
     roof["traffic"] = recorded_traffic(kind, args.workload, args.precision)
     roof["share"] = kms / sum(v[0] for v in prof.values())
@@ -541,13 +694,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == P.FP64 else "f32 values, bf16 8-bit slices, f32/f64 sums",
+        "dtype": "f64" if prec == P.FP64 else "double-float (2 x f32) values, bf16 8-bit slices, f32/f64 sums",
         "data": "synthetic",
-        "config": {"workload": args.workload, "seed": args.seed, "precision": args.precision,
-                   "n_bf": J.n_bf, "n_aux": J.n_aux, "grids": st["grids"], "points": st["points"],
-                   "contractions_per_step": st["contractions"], "classes": "S,T,V,J2,J3" if mask == 31 else mask,
-                   "l2": "working set %.2f GB > 129 MB L2 (no flush needed)" % (J.workspace_bytes(mask) / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": line_config(job, args, world),
+        "job": {"grids": st["grids"], "points": st["points"], "contractions_per_step": st["contractions"],
+                "workspace_gb": J.workspace_bytes(mask) / 1e9, "launches_per_step": st["launches"]},
+        "accuracy": acc,
         "roofline": roof,
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -558,6 +710,8 @@ def main():
         "gpu_launches": st["launches"] * args.steps,
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_serve_block and prec == P.MIXED:
+        line["serve"] = serve_block(P, ctx, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(job)
     if rank == 0:

@@ -192,6 +192,13 @@ psq_status psq_check(psq_job* job, unsigned mask, void* d_workspace, void* strea
  * captured with.  Errors: PSQ_ERR_ARG for a NULL job or a limit out of range. */
 psq_status psq_job_set_wait_limit(psq_job* job, uint64_t ns);
 
+/* Failure-detection test hook (no paper counterpart): while `on`, every psq_compute of a
+ * PSQ_MIXED job raises a flag in its workspace that nothing clears; the contraction's loader
+ * waits for it to clear, gives up when the wait limit runs out and the compute ends with
+ * PSQ_ERR_TIMEOUT in psq_check, exercising the timeout path without a GPU fault.  Errors:
+ * PSQ_ERR_ARG for a NULL job. */
+psq_status psq_job_test_stall(psq_job* job, int on);
+
 /* Diagnostics for step-by-step parity tests. */
 /* Grid g of the PSQ_ALL plan (0 <= g < n_grids; pair grids (A<B) first, then the refined
  * grids (A<B; C)): its atoms (C = -1 for an unrefined pair grid) and point count. */

@@ -71,6 +71,7 @@ SIGNATURES = [
     ("psq_check", _I, [_VP, _U, _VP, _VP]),
     ("psq_job_set_wait_limit", _I, [_VP, ctypes.c_uint64]),
     ("psq_job_set_wave_budget", _I, [_VP, _SZ]),
+    ("psq_job_test_stall", _I, [_VP, _I]),
     ("psq_compute_noalloc", _I, [_VP, _U, ctypes.POINTER(_VP), _VP]),
     ("psq_server_create", _I, [_VP, _VP, _SZ, _I, ctypes.POINTER(_VP)]),
     ("psq_server_submit", _I, [_VP, _VP, _U, ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_uint64)]),
@@ -330,6 +331,10 @@ class Job:
     def set_wave_budget(self, nbytes: int):
         """psq_job_set_wave_budget: the mixed path's operand + packed bytes per wave (0: default)."""
         _check(lib().psq_job_set_wave_budget(self.handle, int(nbytes)))
+
+    def test_stall(self, on: bool):
+        """psq_job_test_stall: raise a flag that nothing clears, so the contraction's wait runs out."""
+        _check(lib().psq_job_test_stall(self.handle, 1 if on else 0))
 
     def set_wait_limit(self, ns: int):
         """psq_job_set_wait_limit: the bound of the contraction's device waits, nanoseconds."""

@@ -187,6 +187,7 @@ struct psq_job {
   std::map<unsigned, int> work_split;  // per mask, chosen by psq_job_autotune
   uint64_t wait_ns = 4000000000ull;    // limit of every bounded device wait (psq_job_set_wait_limit)
   size_t wave_bytes = 0;               // mixed path: operand + packed bytes per wave (0: default)
+  bool test_stall = false;             // failure-detection test hook (psq_job_test_stall)
   std::mutex mu;
   // launch timing: events recorded on the compute stream, read back on request
   struct ProfRec { int kind; cudaEvent_t ev; };
@@ -1428,6 +1429,7 @@ psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_ou
   auto mark = [&](psq_job* j, int kind, cudaStream_t st) { return timing ? ::mark(j, kind, st) : cudaSuccess; };
   CUDA_TRY(mark(job, 0, s));
   CUDA_TRY(cudaMemcpyAsync(ws, P->staging, P->table_bytes, cudaMemcpyHostToDevice, s));
+  if (job->test_stall) CUDA_TRY(cudaMemsetAsync(ws + P->o_status + sizeof(int), 1, sizeof(int), s));
   const LaunchTables t = tables_at(*P, ws);
   double* part = (double*)(ws + P->part_off);
   double* res = (double*)(ws + P->res_off);
@@ -1451,7 +1453,7 @@ psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_ou
       CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
                                   (const int*)(ws + P->o_cb) + wv.cb_off, wv.n_ctas, panels,
                                   (const PairTile*)(ws + P->o_pt), ops, ops_lo, packed, (float2*)part,
-                                  (int*)(ws + P->o_status), job->wait_ns, s));
+                                  (int*)(ws + P->o_status), job->wait_ns, (const int*)(ws + P->o_status) + 1, s));
       CUDA_TRY(mark(job, 3, s));
       CUDA_TRY(launch_reduce_mixed(t.grids, (const MmaBlock*)(ws + P->o_mb), (int)P->mblocks.size(), t.elem_begin,
                                    P->elem_begin[wv.mb0], P->elem_begin[wv.mb1], t.pairs,
@@ -1620,6 +1622,12 @@ psq_status psq_job_set_wave_budget(psq_job* job, size_t bytes) {
   job->plans.clear();
   for (auto& kv : job->graphs) cudaGraphExecDestroy(kv.second);
   job->graphs.clear();
+  return PSQ_OK;
+}
+
+psq_status psq_job_test_stall(psq_job* job, int on) {
+  if (!job) return fail(PSQ_ERR_ARG, "job is NULL");
+  job->test_stall = on != 0;
   return PSQ_OK;
 }
 

@@ -195,11 +195,13 @@ cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels,
 cudaError_t launch_ri_pack(const Panel* panels, int64_t n_jobs, const double* srcA, const double* srcB, int n,
                            uint8_t* packed, cudaStream_t s);
 // CTA b of the persistent contraction works through items [cta_begin[b], cta_begin[b + 1]).
-// wait_ns bounds every wait of the main loops (the drains after a timeout keep a fixed 4 s).
+// wait_ns bounds every wait of the main loops (the drains after a timeout keep a fixed 4 s);
+// hold (may be NULL): a device word that, while nonzero, holds the loader back (the
+// failure-detection test raises it and nothing clears it).
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items,
                                const int* cta_begin, int n_ctas, const Panel* panels, const PairTile* ptiles,
                                const float* ops, const float* ops_lo, const uint8_t* packed, float2* part, int* status,
-                               uint64_t wait_ns, cudaStream_t s);
+                               uint64_t wait_ns, const int* hold, cudaStream_t s);
 // Reduces the elements [e0, e1) of the blocks (prefix sums elem_begin).
 cudaError_t launch_reduce_mixed(const DevGrid* grids, const MmaBlock* blocks, int n_blocks, const int64_t* elem_begin,
                                 int64_t e0, int64_t e1, const short2* rows, const double* rowc, const float2* part,

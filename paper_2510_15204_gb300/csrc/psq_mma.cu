@@ -1,26 +1,26 @@
 // Mixed-precision path of the PS quadrature on sm_103a:
 //  * node tables: the PS grid is a tensor product in (mu, nu, phi) per volume element, so the
 //    per-node trigonometric factors (Section 2.1, eqs 2-6, 10-11) are computed once per grid
-//    row in FP64 (nodes_kernel) and combined per point;
-//  * eval_mixed_kernel: point weights, focal distances and offsets in FP32 from the FP64
-//    tables (the cancellation-free forms need no FP64), the third-centre offset in FP64
-//    (it cancels near that centre), STOs (eq 1), their kinetic operand and the aux
-//    potentials (eq 16, incomplete gamma by its positive series below x = k) in FP32 as
-//    functions of x = zeta r (x from an FP32 hi+lo scale, first-order corrected); every
-//    constant factor of a row is left to FP64;
+//    row in FP64 (nodes_kernel) and stored with double-float (FP32 hi + lo) copies;
+//  * eval_mixed_kernel: point weights, focal distances and offsets in double-float from the
+//    node tables (the cancellation-free forms), the third-centre offset in FP64 (it cancels
+//    near that centre), STOs (eq 1), their kinetic operand and the aux potentials (eq 16,
+//    incomplete gamma by its positive series below x = k) as double-float functions of
+//    x = zeta r and the direction (psq_df.cuh); every constant factor of a row is left to FP64;
 //  * pack_kernel: every operand row that a contraction tile reads whole is scaled by a power
-//    of two per 128-point window (from the window's maximum) and cut into four integer
-//    slices of at most 8 bits (exact in BF16), stored as the tcgen05 shared-memory image;
+//    of two per 128-point window (from the window's maximum) and cut into five integer slices
+//    of at most 8 bits (exact in BF16; 39 bits of the window's largest value), stored as the
+//    tcgen05 shared-memory image (64-byte rows of 32 points, 64-byte swizzle);
 //  * contract_ws_kernel: the weighted contraction of eq 9 on tcgen05 tensor cores.  Packed
-//    tiles arrive by bulk copies; the 3-index operand chi_i chi_j is formed and sliced in
-//    shared memory from staged basis rows.  Per K step of 16 points four MMAs (A slice i
-//    against B slices 0..3-i, contiguous in shared memory) accumulate the slice products of
-//    orders 0..3 into four FP32 TMEM accumulators; all partial sums are integers below 2^23,
-//    so the FP32 accumulation is exact.  After each window the accumulators are scaled back
-//    and added into double-float (FP32 hi + lo) registers; each work item writes its point
-//    range's (hi, lo) sums, and reduce_mixed_kernel adds the ranges in FP64 and applies the
-//    FP64 constants of each row and column (normalisations, powers of zeta, a^3), which the
-//    FP32 values omit.
+//    tiles arrive by bulk copies; the 3-index operand chi_i chi_j is formed (double-float
+//    products) and sliced in shared memory from staged basis rows.  Per K step of 16 points
+//    five MMAs (A slice i against B slices 0..4-i, contiguous in shared memory) accumulate
+//    the slice products of orders 0..4 into five FP32 TMEM accumulators; all partial sums are
+//    integers below 2^24, so the FP32 accumulation is exact.  After each window the
+//    accumulators are scaled back and added into double-float registers; each work item
+//    writes its point range's (hi, lo) sums, and reduce_mixed_kernel adds the ranges in FP64
+//    and applies the FP64 constants of each row and column (normalisations, powers of zeta,
+//    a^3), which the values omit.
 #include "psq_internal.h"
 #include "psq_df.cuh"
 
@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                        const Panel* __restrict__ panels, const PairTile* __restrict__ ptiles,
                        const float* __restrict__ ops, const float* __restrict__ ops_lo,
                        const uint8_t* __restrict__ packed, float2* __restrict__ part, int* __restrict__ status,
-                       uint64_t wait_ns) {
+                       uint64_t wait_ns, const int* __restrict__ hold) {
   using namespace mma;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   ws::Smem& sm = *reinterpret_cast<ws::Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -769,6 +769,20 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     // ------------------------------------------------------------------ loader
     bool run = true;                 // warp-uniform
     int last_a = -1, last_raw = -1;  // last issued chunk / formed window (for the drain)
+    if (hold) {
+      // failure-detection test: a raised flag that nothing clears holds the first copy back
+      // until the wait limit runs out
+      int held = 0;
+      if (lane == 0) {
+        const uint64_t t0 = global_ns();
+        while ((held = *(volatile const int*)hold) != 0 && global_ns() - t0 <= wait_ns) {
+        }
+      }
+      if (__shfl_sync(kFull, held, 0) != 0) {
+        ws::fail(sm, status, 8);
+        run = false;
+      }
+    }
     for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
@@ -1162,10 +1176,10 @@ cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels,
 cudaError_t launch_contract_ws(const DevGrid* grids, const MmaBlock* blocks, const GemmItem* items,
                                const int* cta_begin, int n_ctas, const Panel* panels, const PairTile* ptiles,
                                const float* ops, const float* ops_lo, const uint8_t* packed, float2* part, int* status,
-                               uint64_t wait_ns, cudaStream_t s) {
+                               uint64_t wait_ns, const int* hold, cudaStream_t s) {
   if (n_ctas == 0) return cudaSuccess;
   contract_ws_kernel<<<n_ctas, ws::kThreads, ws_smem_bytes(), s>>>(grids, blocks, items, cta_begin, panels, ptiles, ops,
-                                                                   ops_lo, packed, part, status, wait_ns);
+                                                                   ops_lo, packed, part, status, wait_ns, hold);
   return cudaGetLastError();
 }
 

@@ -444,7 +444,7 @@ extern "C" psq_status psq_ri_eri_mixed(int n, int64_t m, const double* d_B, int6
   if (launch_contract_ws((const DevGrid*)(ws + L.o_grid), (const MmaBlock*)(ws + L.o_blk),
                          (const GemmItem*)(ws + L.o_items), (const int*)(ws + L.o_cb), L.n_ctas, pn, nullptr, nullptr,
                          nullptr, packed, (float2*)(ws + L.o_part), (int*)(ws + L.o_status), 4000000000ull,
-                         s) != cudaSuccess)
+                         nullptr, s) != cudaSuccess)
     return launched();
   if (launch_reduce_mixed((const DevGrid*)(ws + L.o_grid), (const MmaBlock*)(ws + L.o_blk), 1,
                           (const int64_t*)(ws + L.o_eb), 0, nc * nd, (const short2*)(ws + L.o_rows),

@@ -376,6 +376,20 @@ def serving_stream(seed: int = 0, rate: float = 100.0, n_jobs: int = 100, **kw):
     return out
 
 
+def sub_molecule(job: Job, keep, name: str = None) -> Job:
+    """The sub-molecule of the atoms `keep` (in the given order): their shells and the grid
+    specs of their pairs, renumbered; the same classes."""
+    keep = list(keep)
+    idx = {a: i for i, a in enumerate(keep)}
+    atoms = [job.atoms[a] for a in keep]
+    basis = [(idx[s[0]],) + tuple(s[1:]) for s in job.basis if s[0] in idx]
+    aux = [(idx[s[0]],) + tuple(s[1:]) for s in job.aux if s[0] in idx]
+    basis.sort(key=lambda s: s[0])
+    aux.sort(key=lambda s: s[0])
+    specs = [job.spec_for_pair(keep[i], keep[j]) for i in range(len(keep)) for j in range(i + 1, len(keep))]
+    return Job(name or "%s_atoms%s" % (job.name, "".join(str(a) for a in keep)), atoms, basis, aux, specs, job.mask)
+
+
 WORKLOADS = {
     "h2_fp64": h2_fp64,
     "triatomic_oh2": triatomic_oh2,

@@ -56,7 +56,9 @@ def test_noalloc_mixed_on_reused_scratch():
     import torch
     import paper_2510_15204_gb300 as P
     ctx = P.Context(0)
-    J = P.Job.from_synth(ctx, synth.h2_fp64(1), P.MIXED)
+    job = synth.h2_fp64(1)
+    job.specs = [(12, 8, 6, 4, 4, 4, 3)]  # 36,864 points: the mixed workspace within the 64 MiB scratch
+    J = P.Job.from_synth(ctx, job, P.MIXED)
     mask = oracle.ALL
     assert J.workspace_bytes(mask) <= 64 << 20
     ws, ref_out = J.alloc(mask)
