@@ -132,6 +132,12 @@ PSQ_DF_FN df pow_i(df x, int n) {
   return r;
 }
 
+// c x^n, the factor c taken first (with x < 1 no intermediate falls below the result).
+PSQ_DF_FN df mul_pow(df c, df x, int n) {
+  for (int i = 0; i < n; ++i) c = mul(c, x);
+  return c;
+}
+
 PSQ_DF_FN double to_double(df x) { return (double)x.h + (double)x.l; }
 
 // Constants of e^-x: ln 2 / 64 = kL1 + kL2 + kL3 with kL1 of 10 significant bits (k * kL1
@@ -216,6 +222,14 @@ PSQ_DF_FN void real_ylm(int lmax, df ux, df uy, df uz, df* Y) {
 //   gamma(k, x) = x^k e^-x sum_j x^j / (k (k+1) ... (k+j)) (no cancellation); above, (k-1)! -
 //   Gamma(k, x).  ex = e^-x, ix = 1/x; fact[k] = k! as (hi, lo); rcp[k] = 1/k in FP32 (k < 128).
 PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fact, const float* rcp) {
+  if (ex.h == 0.0f) {
+    // e^-x below FP32 range (x >= 87; grids of distant pairs reach x ~ 1e5, where the finite
+    // sums below would overflow): the upper incomplete gamma terms vanish, V^P is the
+    // multipole term (k-1)!/x^(l+1), chi and lap chi are 0
+    if (kind != 2) return mk(0.0f);
+    const int k1 = n + l + 2;
+    return mul_pow(df{fact[k1 - 1].x, fact[k1 - 1].y}, ix, l + 1);
+  }
   if (kind == 2) {
     const int k1 = n + l + 2, k2 = n - l + 1;
     df inner;
@@ -242,7 +256,7 @@ PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fa
         s = add_same(s, t);
       }
       const df q = sub(mk(1.0f), mul(ex, s));  // regularised lower gamma, >= 1/2 for x >= k
-      inner = mul(mul(df{fact[k1 - 1].x, fact[k1 - 1].y}, q), pow_i(ix, l + 1));
+      inner = mul_pow(mul(df{fact[k1 - 1].x, fact[k1 - 1].y}, q), ix, l + 1);
     }
     df t = mk(1.0f), s = mk(1.0f);
     for (int j = 1; j < k2; ++j) {

@@ -95,9 +95,18 @@ def test_radial_factors(run, kind):
     for (n, l) in [(1, 0), (2, 0), (2, 1), (3, 2), (4, 3), (5, 4), (6, 5), (3, 0), (7, 6)]:
         for x in (1e-3, 0.05, 0.4, 1.0, 2.9, 3.0, 3.1, n + l + 1.5, n + l + 2.0, n + l + 2.5, 9.0, 17.0, 40.0, 60.0):
             cases.append((n, l, x))
+    # far points of refined grids around distant pairs: x up to ~1e5 (sums must not overflow)
+    cases += [(n, l, x) for (n, l) in [(1, 0), (5, 4), (7, 6), (12, 6)] for x in (90.0, 500.0, 5e4, 3e6)]
     got = run(["radial %d %d %d %.17g" % (kind, n, l, x) for (n, l, x) in cases])
     for (n, l, x), g in zip(cases, got):
+        assert all(math.isfinite(v) for v in g), (kind, n, l, x, g)
         ref, scale = _radial_ref(kind, n, l, x)
+        if x >= 87 and kind != 2:
+            # e^-x flushed to 0 past x = 87: the exact value is below 1e-20 of the function's
+            # largest, x^(n-1) e^-x at x = n - 1
+            top = max(1.0, float((n - 1) ** (n - 1) * mpmath.exp(-(n - 1))))
+            assert g[0] == 0.0 and abs(float(ref)) < 1e-20 * top, (kind, n, l, x, g[0], float(ref))
+            continue
         scale = abs(float(ref)) if scale is None else float(scale)
         assert abs(g[0] - float(ref)) <= TOL * scale + FLOOR, (kind, n, l, x, g[0], float(ref))
 

@@ -44,6 +44,8 @@ def test_fivez_sampled_blocks(ref, precision, tol):
     J.check(oracle.ALL, ws)
     torch.cuda.synchronize()
     got = {k: v.cpu().numpy() for k, v in out.items()}
+    for k, v in got.items():  # every element, not only the sampled blocks
+        assert np.isfinite(v).all(), (k, int((~np.isfinite(v)).sum()))
     del ws
     torch.cuda.empty_cache()
     bs, ax = _fn_slices(job.basis, job.n_atoms), _fn_slices(job.aux, job.n_atoms)
