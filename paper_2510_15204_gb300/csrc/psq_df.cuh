@@ -107,6 +107,16 @@ PSQ_DF_FN df div_f(df x, float d) {
   return fast_two_sum(q, __fdividef(r, d));
 }
 
+// x / k for a small positive integer k, with rcp[k] ~ 1/k (FP32): quotient from the table
+// reciprocal, the exact residual x - q k divided once more (no SFU instruction).
+PSQ_DF_FN df div_k(df x, int k, const float* rcp) {
+  const float r = rcp[k];
+  const float q = __fmul_rn(x.h, r);
+  const df p = two_prod(q, (float)k);
+  const float e = __fadd_rn(__fsub_rn(__fsub_rn(x.h, p.h), p.l), x.l);
+  return fast_two_sum(q, __fmul_rn(e, r));
+}
+
 // x / y.
 PSQ_DF_FN df div(df x, df y) {
   const float q = __fdividef(x.h, y.h);
@@ -150,7 +160,8 @@ struct ExpConsts {
 // x = k ln2/64 + r, |r| <= ln2/128, e^-x = 2^-(k/64) e^-r with k = 64 q + j.
 PSQ_DF_FN df exp_neg(df x, const ExpConsts& c, const float2* tab) {
   if (!(x.h < 87.0f)) return mk(0.0f);  // below 1.7e-38: zero at this precision
-  const float kf = rintf(__fmul_rn(x.h, c.inv));
+  // nearest integer of x 64/ln2 (< 2^13) by the FP32 magic number 1.5 * 2^23
+  const float kf = __fsub_rn(__fadd_rn(__fmul_rn(x.h, c.inv), 12582912.0f), 12582912.0f);
   const int k = (int)kf;
   // x - k c1 is exact (k c1 has at most 24 bits and lies within a factor 2 of x_h)
   df r = two_sum(__fsub_rn(x.h, __fmul_rn(kf, c.c1)), x.l);
@@ -180,7 +191,7 @@ PSQ_DF_FN df add_same(df x, df y) {
 // Unnormalised real harmonics Yu_lm(u) = Q_l^|m|(u_z) {Re, Im}(u_x + i u_y)^|m| (the norms K_lm
 // are left to the FP64 row constants), index l*l + l + m, l <= lmax <= 6: Q_m^m = (2m-1)!!,
 // Q_{m+1}^m = (2m+1) u_z Q_m^m, (l-m) Q_l^m = (2l-1) u_z Q_{l-1}^m - (l+m-1) Q_{l-2}^m.
-PSQ_DF_FN void real_ylm(int lmax, df ux, df uy, df uz, df* Y) {
+PSQ_DF_FN void real_ylm(int lmax, df ux, df uy, df uz, df* Y, const float* rcp) {
   df C[7], S[7];
   C[0] = mk(1.0f);
   S[0] = mk(0.0f);
@@ -200,7 +211,7 @@ PSQ_DF_FN void real_ylm(int lmax, df ux, df uy, df uz, df* Y) {
         q = mul_f(uz, (float)(2 * m + 1) * dfact);
       } else {
         const df a = mul_f(mul(uz, q1), (float)(2 * l - 1));
-        q = div_f(sub(a, mul_f(q2, (float)(l + m - 1))), (float)(l - m));
+        q = div_k(sub(a, mul_f(q2, (float)(l + m - 1))), l - m, rcp);
       }
       if (l > m) { q2 = q1; q1 = q; }
       const int base = l * l + l;
@@ -234,10 +245,10 @@ PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fa
     const int k1 = n + l + 2, k2 = n - l + 1;
     df inner;
     if (x.h < (float)k1) {
-      df t = div_f(mk(1.0f), (float)k1), s = t;
+      df t = div_k(mk(1.0f), k1, rcp), s = t;
       int j = 1;
-      for (; j < 200; ++j) {  // double-float terms while they reach 2^-24 of the sum
-        t = div_f(mul(t, x), (float)(k1 + j));
+      for (; j < 100; ++j) {  // double-float terms while they reach 2^-24 of the sum
+        t = div_k(mul(t, x), k1 + j, rcp);
         s = add_same(s, t);
         if (t.h < 5.9604645e-8f * s.h) break;
       }
@@ -252,7 +263,7 @@ PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fa
     } else {
       df t = mk(1.0f), s = mk(1.0f);
       for (int j = 1; j < k1; ++j) {
-        t = div_f(mul(t, x), (float)j);
+        t = div_k(mul(t, x), j, rcp);
         s = add_same(s, t);
       }
       const df q = sub(mk(1.0f), mul(ex, s));  // regularised lower gamma, >= 1/2 for x >= k
@@ -260,7 +271,7 @@ PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fa
     }
     df t = mk(1.0f), s = mk(1.0f);
     for (int j = 1; j < k2; ++j) {
-      t = div_f(mul(t, x), (float)j);
+      t = div_k(mul(t, x), j, rcp);
       s = add_same(s, t);
     }
     const df outer = mul(mul(mul(df{fact[k2 - 1].x, fact[k2 - 1].y}, ex), s), pow_i(x, l));

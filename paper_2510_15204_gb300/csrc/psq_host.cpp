@@ -886,19 +886,60 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
             for (int y = 0; y < tn; ++y) items.push_back(GemmItem{bi, x, y, c});
       }
       part_max = std::max(part_max, pt);
-      std::stable_sort(items.begin(), items.end(),
-                       [&](const GemmItem& x, const GemmItem& y) { return item_cost(x) > item_cost(y); });
+      // Gangs: the items of one (block, A tile, window range) read the same packed A chunks,
+      // one item per B tile.  A gang's items go to different CTAs at the same depth of their
+      // queues, so that they run at about the same time and the A chunks come from L2 after
+      // the first read (a refined grid's A panel exceeds the L2).  Gangs by cost, largest
+      // first; each item of a gang to the CTA with the least cost so far (LPT over gangs).
+      std::stable_sort(items.begin(), items.end(), [&](const GemmItem& x, const GemmItem& y) {
+        if (x.block != y.block) return x.block < y.block;
+        if (x.tm != y.tm) return x.tm < y.tm;
+        if (x.chunk != y.chunk) return x.chunk < y.chunk;
+        return x.tn < y.tn;
+      });
+      std::vector<std::pair<size_t, size_t>> gangs;  // [begin, end) in items
+      for (size_t i = 0; i < items.size();) {
+        size_t k = i + 1;
+        while (k < items.size() && items[k].block == items[i].block && items[k].tm == items[i].tm &&
+               items[k].chunk == items[i].chunk)
+          ++k;
+        gangs.push_back({i, k});
+        i = k;
+      }
+      auto gang_cost = [&](const std::pair<size_t, size_t>& g) {
+        double c = 0;
+        for (size_t i = g.first; i < g.second; ++i) c += item_cost(items[i]);
+        return c;
+      };
+      std::stable_sort(gangs.begin(), gangs.end(), [&](const std::pair<size_t, size_t>& x,
+                                                        const std::pair<size_t, size_t>& y) {
+        return gang_cost(x) > gang_cost(y);
+      });
       wv.n_ctas = (int)std::min<int64_t>((int64_t)items.size(), j->ctx->sm_count);
       std::vector<std::vector<GemmItem>> per(wv.n_ctas);
       std::vector<std::pair<double, int>> heap;  // (cost so far, CTA), min-heap
       for (int b = 0; b < wv.n_ctas; ++b) heap.push_back({0.0, b});
       auto cmp = [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x > y; };
       std::make_heap(heap.begin(), heap.end(), cmp);
-      for (const GemmItem& it : items) {
-        std::pop_heap(heap.begin(), heap.end(), cmp);
-        per[heap.back().second].push_back(it);
-        heap.back().first += item_cost(it);
-        std::push_heap(heap.begin(), heap.end(), cmp);
+      std::vector<std::pair<double, int>> taken;
+      for (const auto& g : gangs) {
+        // the gang's items to the least loaded CTAs, one each (a gang larger than the CTA
+        // count wraps around)
+        for (size_t i = g.first; i < g.second;) {
+          taken.clear();
+          for (; i < g.second && !heap.empty(); ++i) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto slot = heap.back();
+            heap.pop_back();
+            per[slot.second].push_back(items[i]);
+            slot.first += item_cost(items[i]);
+            taken.push_back(slot);
+          }
+          for (const auto& t : taken) {
+            heap.push_back(t);
+            std::push_heap(heap.begin(), heap.end(), cmp);
+          }
+        }
       }
       wv.cb_off = (int)P.cta_begin.size();
       P.cta_begin.push_back((int)P.mitems.size());

@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
       const int s0 = c == 0 ? g.shb_A0 : g.shb_B0, s1 = c == 0 ? g.shb_A1 : g.shb_B1;
       if (s1 <= s0) continue;
       const df* u = c == 0 ? uA : uB;
-      dfa::real_ylm(shells_lmax_f(t.bshell, s0, s1), u[0], u[1], u[2], Y);
+      dfa::real_ylm(shells_lmax_f(t.bshell, s0, s1), u[0], u[1], u[2], Y, c_rcpf);
       const int roff = c == 0 ? 0 : g.nFA;
       eval_shells_df(t.bshell, xi + (c == 0 ? 0 : nbA), s0, s1, c == 0 ? rhoA : rhoB, Y, bh, bl, ld, p,
                      g.row_F >= 0 ? g.row_F + roff : -1, 0, g.row_L >= 0 ? g.row_L + roff : -1, 1, etab);
@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(128) eval_mixed_kernel(LaunchTables t, const N
       if (atom == g.A) { u = uA; rho = rhoA; }
       else if (atom == g.B) { u = uB; rho = rhoB; }
       else { u = uC; rho = rC; }
-      dfa::real_ylm(shells_lmax_f(t.ashell, s0, s1), u[0], u[1], u[2], Y);
+      dfa::real_ylm(shells_lmax_f(t.ashell, s0, s1), u[0], u[1], u[2], Y, c_rcpf);
       eval_shells_df(t.ashell, xi + nbA + nbB + (c == 0 ? 0 : na0), s0, s1, rho, Y, bh, bl, ld, p,
                      g.row_G >= 0 ? g.row_G + roff : -1, 0, g.row_U >= 0 ? g.row_U + roff : -1, 2, etab);
       int nf = 0;
@@ -444,20 +444,36 @@ __device__ __forceinline__ float pow2f(int k) {
 
 namespace mma {
 
+// JOIN: the digit after which the lo parts join the remainder.  JOIN = 2 for normalised pairs
+// (|lo| <= 2^-24 |hi|; s3 <= 256); JOIN = 1 for products left unnormalised (|lo| <= 3 2^-24
+// |hi|: the join adds at most 1.5 to s2, which stays <= 130, and rounds at 2^-17 of s2's unit,
+// 2^-40 of the window's largest value).
+// Nearest integer (ties to even) of |x| < 2^22 by the FP32 magic number 1.5 * 2^23: x + M lies
+// in [2^23, 2^24), where the spacing is 1, so the addition rounds x to an integer and the
+// subtraction is exact (two full-rate adds instead of a conversion-pipe instruction).
+__device__ __forceinline__ float rne_small(float x) { return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f); }
+
+// BF16x2 bits of two floats that are exact in BF16 (integers of at most 8 significant bits:
+// their low 16 bits are zero), first value in the low half.
+__device__ __forceinline__ uint32_t pack_bf16_exact(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+template <int JOIN>
 __device__ __forceinline__ void slice8_df(const float* vh, const float* vl, float sc, uint4* w) {
+  constexpr float kJoin = JOIN == 2 ? 16777216.0f : 65536.0f;  // 256^JOIN
   uint32_t o[kSlices][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float r0 = vh[2 * q] * sc, r1 = vh[2 * q + 1] * sc;
-    const float l0 = vl[2 * q] * sc * 16777216.0f, l1 = vl[2 * q + 1] * sc * 16777216.0f;
+    const float l0 = vl[2 * q] * sc * kJoin, l1 = vl[2 * q + 1] * sc * kJoin;
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) {
-      const float a0 = rintf(r0), a1 = rintf(r1);
-      const __nv_bfloat162 p = __floats2bfloat162_rn(a0, a1);
-      o[k][q] = *reinterpret_cast<const uint32_t*>(&p);
+      const float a0 = rne_small(r0), a1 = rne_small(r1);
+      o[k][q] = pack_bf16_exact(a0, a1);
       r0 = (r0 - a0) * 256.0f;
       r1 = (r1 - a1) * 256.0f;
-      if (k == 2) {
+      if (k == JOIN) {
         r0 += l0;
         r1 += l1;
       }
@@ -530,7 +546,7 @@ __device__ __forceinline__ void pack_store(const PackPos& P, const Panel& pn, co
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     uint4 wv[kSlices];
-    slice8_df(h + 8 * j, l + 8 * j, sc, wv);
+    slice8_df<2>(h + 8 * j, l + 8 * j, sc, wv);
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(P.r, 2 * (P.qq & 1) + j)) = wv[k];
   }
@@ -611,6 +627,15 @@ __global__ void __launch_bounds__(128) ri_pack_kernel(const Panel* __restrict__ 
   pack_store(P, pn, h, l, packed);
 }
 
+// (xh + xl)(yh + yl) as hi = fl(xh yh) and the unnormalised lo = the exact error of that
+// product plus the cross terms (|lo| <= 3 2^-24 |hi|; the lo lo term, below 2^-48, dropped).
+__device__ __forceinline__ void prod_unnorm(float xh, float xl, float yh, float yl, float& h, float& l) {
+  h = __fmul_rn(xh, yh);
+  float e = __fmaf_rn(xh, yh, -h);
+  e = __fmaf_rn(xh, yl, e);
+  l = __fmaf_rn(xl, yh, e);
+}
+
 // ------------------------------------------------------------------ warp-specialised contraction
 //
 // One persistent CTA per SM, 512 threads, working through tiles (128 A rows x <= 48 B
@@ -650,7 +675,7 @@ struct Smem {
   int eb[2][mma::kTileN];
   float sbw[8][mma::kTileN];  // fold warp k: the column scales of the current window
   alignas(8) uint64_t a_full[mma::kStages], b_ready[mma::kStages], stage_free[mma::kStages];
-  uint64_t tmem_full[2], tmem_free[2], raw_full[2], raw_free[2];
+  uint64_t tmem_full[2], tmem_free[2], raw_full[2], raw_free[2], eb_free[2];
   uint64_t drain;
   uint32_t tmem_base;
   int abort;
@@ -753,6 +778,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       ws::mbar_init(&sm.tmem_free[s], 8);
       ws::mbar_init(&sm.raw_full[s], 1);
       ws::mbar_init(&sm.raw_free[s], 6);
+      ws::mbar_init(&sm.eb_free[s], 8);
     }
     ws::mbar_init(&sm.drain, 1);
     sm.abort = 0;
@@ -872,7 +898,6 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         const int nck = ws::chunks_in(q, win);
         const int rb = rw & 1, set = w & 1;
         bool ok = ws::wait(&sm.raw_full[rb], (rw >> 1) & 1, &sm.abort, wait_ns);
-        if (ok && w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort, wait_ns);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 5); break; }
         const int64_t wleft = q.K - (int64_t)kWinPts * win;  // points of the window that exist
@@ -897,18 +922,13 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             *reinterpret_cast<float4*>(bl) = *reinterpret_cast<const float4*>(yl);
             *reinterpret_cast<float4*>(bl + 4) = *reinterpret_cast<const float4*>(yl + 4);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const df v = dfa::mul(df{a[i], al[i]}, df{bb[i], bl[i]});
-              vh[cc][i] = v.h;
-              vl[cc][i] = v.l;
-            }
+            for (int i = 0; i < 8; ++i) prod_unnorm(a[i], al[i], bb[i], bl[i], vh[cc][i], vl[cc][i]);
           } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-              df v = dfa::mk(0.0f);
-              if (i < left) v = dfa::mul(df{xh[i], xl[i]}, df{yh[i], yl[i]});
-              vh[cc][i] = v.h;
-              vl[cc][i] = v.l;
+              vh[cc][i] = 0.0f;
+              vl[cc][i] = 0.0f;
+              if (i < left) prod_unnorm(xh[i], xl[i], yh[i], yl[i], vh[cc][i], vl[cc][i]);
             }
           }
 #pragma unroll
@@ -918,6 +938,11 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 1));
         mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 2));
         const int e = row_exponent(mx);
+        // the column exponents of this set were last read by the fold of window w - 2, which
+        // releases them (eb_free) as soon as it has copied them: the fold stays off this path
+        const bool okb = w < 2 || ws::wait(&sm.eb_free[set], ((w - 2) >> 1) & 1, &sm.abort, wait_ns);
+        run = __all_sync(kFull, okb && !ws::aborted(sm));
+        if (!run) { ws::fail(sm, status, 5); break; }
         if (g == 0) sm.eb[set][col] = e;
         const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
 #pragma unroll
@@ -931,7 +956,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
               ws::fail(sm, status, 5);
             } else {
               uint4 wv[kSlices];
-              slice8_df(vh[cc], vl[cc], sc, wv);
+              slice8_df<1>(vh[cc], vl[cc], sc, wv);
 #pragma unroll
               for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(sm.b[s][k] + swz(col, g)) = wv[k];
               fence_async_smem();
@@ -1034,6 +1059,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         if (lane < 24) sbw[my_col] = pow2f((pb ? eb_lane : sm.eb[set][my_col]) - 7);
         const float sa = pow2f(ea - 7);
         __syncwarp();
+        if (lane == 0) ws::mbar_arrive(&sm.eb_free[set]);  // the producers may refill eb[set]
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * 256u;
         // a warp whose 32 rows are all past the tile's last real row has nothing to fold
         if (quad * 32 < rows_valid) {
@@ -1049,14 +1075,15 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
               for (int j = 0; j < 8; ++j) {
                 const int qq = 8 * gi + j;
                 const float sc = sa * sbw[c0 + j];  // 2^(e_a + e_b - 14)
-                // orders 0, 1, 2 (exact integers times powers of two) into the double-float sum
-                // through TwoSums, orders 3 and 4 as one FP32 term
+                // orders 0 and 1 (exact integers times powers of two) into the double-float sum
+                // through TwoSums; orders 2-4, at most 2^-15 of order 0, as one FP32 term into
+                // the lo word (rounded at 2^-39 of the window's largest)
                 const df s0 = dfa::two_sum(H[qq], o[0][j] * sc);
                 const df s1 = dfa::two_sum(s0.h, o[1][j] * (sc * 0.00390625f));
-                const df s2 = dfa::two_sum(s1.h, o[2][j] * (sc * 1.52587890625e-5f));
-                const float tail = fmaf(o[4][j], 2.3283064365386963e-10f, o[3][j] * 5.9604644775390625e-8f) * sc;
-                const float lo = L[qq] + ((s0.l + s1.l) + (s2.l + tail));
-                const df r = dfa::fast_two_sum(s2.h, lo);
+                const float tail =
+                    fmaf(o[2][j], 1.52587890625e-5f, fmaf(o[4][j], 2.3283064365386963e-10f, o[3][j] * 5.9604644775390625e-8f)) * sc;
+                const float lo = L[qq] + ((s0.l + s1.l) + tail);
+                const df r = dfa::fast_two_sum(s1.h, lo);
                 H[qq] = r.h;
                 L[qq] = r.l;
               }

@@ -77,7 +77,7 @@ int main() {
       double ux, uy, uz;
       in >> L >> ux >> uy >> uz;
       df Y[49];
-      psq::dfa::real_ylm(L, split(ux), split(uy), split(uz), Y);
+      psq::dfa::real_ylm(L, split(ux), split(uy), split(uz), Y, rcp);
       for (int i = 0; i < (L + 1) * (L + 1); ++i) put(Y[i]);
     } else {
       continue;
