@@ -526,7 +526,16 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
     }
     // chunking: enough CTAs for several waves, chunks of at least 2048 points
     int64_t tiles = 0;
-    for (auto& b : P.gblocks) tiles += (int64_t)((b.m + kTile - 1) / kTile) * ((b.n + kTile - 1) / kTile);
+    // output tile per block: balanced row tiles of <= 64 rows, then balanced column tiles of
+    // <= min(256, 1024 / rows) columns (little padding; no FP64 operation on padding)
+    for (auto& b : P.gblocks) {
+      const int ntm = (b.m + kFpTileRows - 1) / kFpTileRows;
+      b.tile_m = std::max(1, (b.m + ntm - 1) / ntm);
+      const int tn_max = std::max(1, std::min(kFpTileCols, kFpTileOut / b.tile_m));
+      const int ntn = (b.n + tn_max - 1) / tn_max;
+      b.tile_n = std::max(1, (b.n + ntn - 1) / ntn);
+      tiles += (int64_t)ntm * ntn;
+    }
     const int64_t want = 2LL * kSmCount * P.work_split;
     const int cglob = (int)std::max<int64_t>(1, tiles > 0 ? (want + tiles - 1) / tiles : 1);
     for (size_t bi = 0; bi < P.gblocks.size(); ++bi) {
@@ -539,7 +548,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       b.n_chunks = std::max(1, b.n_chunks);
       b.part_off = part;
       part += (int64_t)b.n_chunks * b.m * b.n;
-      const int tm = (b.m + kTile - 1) / kTile, tn = (b.n + kTile - 1) / kTile;
+      const int tm = (b.m + b.tile_m - 1) / b.tile_m, tn = (b.n + b.tile_n - 1) / b.tile_n;
       for (int c = 0; c < b.n_chunks; ++c)
         for (int x = 0; x < tm; ++x)
           for (int y = 0; y < tn; ++y) P.items.push_back(GemmItem{(int)bi, x, y, c});

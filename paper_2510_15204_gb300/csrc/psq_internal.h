@@ -11,7 +11,6 @@ namespace psq {
 constexpr int kMaxL = 6;    // highest angular momentum of a basis or aux shell
 constexpr int kMaxN = 12;   // highest principal quantum number
 constexpr int kMaxQ = 16;   // Gauss-Legendre points per dimension
-constexpr int kTile = 32;   // FP64 contraction output tile (rows and columns)
 
 // One shell of STO or aux functions (eq 1), with its radial normalisation.
 struct DevShell {
@@ -126,9 +125,11 @@ struct GemmBlock {
   int pair_off;     // into the pair table (b_mode 1): pairs of F rows
   int d_row;        // weight row (w, w/r_A, w/r_B or w/r_C)
   int n_chunks;     // point range split into n_chunks partial sums
+  int tile_m, tile_n;  // output tile of one CTA (tile_m <= kFpTileRows, tile_n <= kFpTileCols, <= 1024 outputs)
   int64_t res_off;  // m x n FP64 result
   int64_t part_off; // n_chunks x m x n FP64 partial sums
 };
+constexpr int kFpTileRows = 64, kFpTileCols = 256, kFpTileOut = 1024;
 
 struct GemmItem { int block, tm, tn, chunk; };
 

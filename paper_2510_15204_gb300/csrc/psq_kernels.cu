@@ -267,8 +267,16 @@ cudaError_t launch_eval_fp64(const LaunchTables& t, double* ops, int /*kinds*/, 
   return cudaGetLastError();
 }
 
-// Weighted contraction, FP64 (eq 9): one CTA per (block, 32x32 output tile, point chunk);
-// partial sums go to their own slot, so the result does not depend on scheduling.
+// Weighted contraction, FP64 (eq 9): one CTA per (block, output tile, point chunk); the tile
+// (tile_m x tile_n, chosen per block so that the block is covered with little padding) is
+// mapped densely onto 256 threads, thread t owning outputs t, t + 256, ... of the tile's real
+// rows x columns (row-major).  Per 16-point step the weighted A rows and the B columns (basis
+// rows, or products of two basis rows) are formed once in shared memory; on GB300 the FP64
+// pipe (a warp's DFMA every ~16 SM cycles) is the bound, so each output's sub-sum reads both
+// operands from shared memory and no FP64 operation goes to padding.  Sub-sums of each step
+// join the running sums (small outer-region terms are not absorbed one by one), and partial
+// sums go to their own slot, so the result does not depend on scheduling.
+constexpr int kFpPts = 16;
 __global__ void __launch_bounds__(256) contract_fp64_kernel(LaunchTables t, const double* __restrict__ ops,
                                                              double* __restrict__ part) {
   const GemmItem it = t.items[blockIdx.x];
@@ -279,63 +287,61 @@ __global__ void __launch_bounds__(256) contract_fp64_kernel(LaunchTables t, cons
   const int64_t csz = (K + b.n_chunks - 1) / b.n_chunks;
   const int64_t k0 = (int64_t)it.chunk * csz;
   const int64_t k1 = min(K, k0 + csz);
-  __shared__ double As[kTile][kTile + 1];
-  __shared__ double Bs[kTile][kTile + 1];
-  __shared__ short2 pr[kTile];
-  const int r0 = it.tm * kTile, c0 = it.tn * kTile;
-  if (threadIdx.x < kTile) {
-    short2 q = make_short2(0, 0);
-    if (b.b_mode == 1 && c0 + (int)threadIdx.x < b.n) q = t.pairs[b.pair_off + c0 + threadIdx.x];
-    pr[threadIdx.x] = q;
-  }
+  __shared__ double As[kFpPts][kFpTileRows];
+  __shared__ double Bs[kFpPts][kFpTileCols];
+  __shared__ short2 pr[kFpTileCols];
+  const int r0 = it.tm * b.tile_m, c0 = it.tn * b.tile_n;
+  const int rows = min(b.tile_m, b.m - r0), cols = min(b.tile_n, b.n - c0);
+  for (int c = threadIdx.x; c < cols; c += blockDim.x)
+    pr[c] = b.b_mode == 1 ? t.pairs[b.pair_off + c0 + c] : make_short2(0, 0);
   const double* drow = base + (int64_t)b.d_row * ld;
-  const int tm = threadIdx.x / 16, tn = threadIdx.x % 16;
-  double acc00 = 0, acc01 = 0, acc10 = 0, acc11 = 0;
+  const int nout = rows * cols;
+  int orow[4], ocol[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int o = threadIdx.x + 256 * q;
+    orow[q] = o < nout ? o / cols : 0;
+    ocol[q] = o < nout ? o - (o / cols) * cols : 0;
+  }
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   __syncthreads();
-  for (int64_t k = k0; k < k1; k += kTile) {
-    for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-      const int r = e / kTile, pp = e % kTile;
+  for (int64_t k = k0; k < k1; k += kFpPts) {
+    // operands of this step: A rows x points, B columns x points (zeros past the chunk)
+    for (int e = threadIdx.x; e < rows * kFpPts; e += blockDim.x) {
+      const int r = e / kFpPts, pp = e - r * kFpPts;
       const int64_t kk = k + pp;
-      double av = 0.0, bv = 0.0;
+      As[pp][r] = kk < k1 ? base[(int64_t)(b.a_row + r0 + r) * ld + kk] * drow[kk] : 0.0;
+    }
+    for (int e = threadIdx.x; e < cols * kFpPts; e += blockDim.x) {
+      const int c = e / kFpPts, pp = e - c * kFpPts;
+      const int64_t kk = k + pp;
+      double bv = 0.0;
       if (kk < k1) {
-        if (r0 + r < b.m) av = base[(int64_t)(b.a_row + r0 + r) * ld + kk] * drow[kk];
-        if (c0 + r < b.n) {
-          if (b.b_mode == 0) {
-            bv = base[(int64_t)(b.b_row + c0 + r) * ld + kk];
-          } else {
-            const short2 q = pr[r];
-            bv = base[(int64_t)(b.b_row + q.x) * ld + kk] * base[(int64_t)(b.b_row + q.y) * ld + kk];
-          }
+        if (b.b_mode == 0) {
+          bv = base[(int64_t)(b.b_row + c0 + c) * ld + kk];
+        } else {
+          const short2 q = pr[c];
+          bv = base[(int64_t)(b.b_row + q.x) * ld + kk] * base[(int64_t)(b.b_row + q.y) * ld + kk];
         }
       }
-      As[pp][r] = av;
-      Bs[pp][r] = bv;
+      Bs[pp][c] = bv;
     }
     __syncthreads();
-    // sub-sums of the tile's 32 points first, so that small outer-region terms are not
-    // absorbed one by one into a large running sum
-    double s00 = 0, s01 = 0, s10 = 0, s11 = 0;
-#pragma unroll 8
-    for (int pp = 0; pp < kTile; ++pp) {
-      const double a0 = As[pp][2 * tm], a1 = As[pp][2 * tm + 1];
-      const double b0 = Bs[pp][2 * tn], b1 = Bs[pp][2 * tn + 1];
-      s00 = fma(a0, b0, s00);
-      s01 = fma(a0, b1, s01);
-      s10 = fma(a1, b0, s10);
-      s11 = fma(a1, b1, s11);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (threadIdx.x + 256 * q < nout) {
+        double sq = 0.0;
+#pragma unroll
+        for (int pp = 0; pp < kFpPts; ++pp) sq = fma(As[pp][orow[q]], Bs[pp][ocol[q]], sq);
+        acc[q] += sq;
+      }
     }
-    acc00 += s00;
-    acc01 += s01;
-    acc10 += s10;
-    acc11 += s11;
     __syncthreads();
   }
   double* out = part + b.part_off + (int64_t)it.chunk * b.m * b.n;
-  const int r = r0 + 2 * tm, c = c0 + 2 * tn;
-  if (r < b.m && c < b.n) out[(int64_t)r * b.n + c] = acc00;
-  if (r < b.m && c + 1 < b.n) out[(int64_t)r * b.n + c + 1] = acc01;
-  if (r + 1 < b.m && c < b.n) out[(int64_t)(r + 1) * b.n + c] = acc10;
-  if (r + 1 < b.m && c + 1 < b.n) out[(int64_t)(r + 1) * b.n + c + 1] = acc11;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (threadIdx.x + 256 * q < nout) out[(int64_t)(r0 + orow[q]) * b.n + c0 + ocol[q]] = acc[q];
 }
 
 cudaError_t launch_contract_fp64(const LaunchTables& t, const double* ops, double* part, cudaStream_t s) {
