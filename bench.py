@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-ri", action="store_true", help="skip timing the RI 4-index assembly")
     ap.add_argument("--serve", action="store_true", help="serving benchmark instead of the step benchmark")
     ap.add_argument("--scan", action="store_true", help="Fig. 6 displacement scans through the serving loop")
+    ap.add_argument("--ri-sizes", default=None,
+                    help="n,m: time the RI 4-index assembly alone on seeded synthetic (P|Q) (n x n) and (P|ij) "
+                         "(n x m) matrices")
     ap.add_argument("--rates", default="10,20,50,100,200,500", help="serving: Poisson arrival rates (jobs/s)")
     ap.add_argument("--jobs", type=int, default=300, help="serving: jobs per rate")
     ap.add_argument("--baseline-jobs", type=int, default=6, help="serving: jobs timed on the per-job FP64 path")
@@ -345,7 +348,7 @@ def time_ri(J2, J3, stream, reps=20):
 
 
 def recorded_traffic(kernel, workload, precision):
-    """DRAM bytes per launch of `kernel` from profiles/traffic.txt, if recorded for the current
+    """DRAM bytes of `kernel` per bench step from profiles/traffic.txt, if recorded for the current
     kernel source (null once the source changed since the counters were taken)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -545,10 +548,32 @@ def scan_main(args):
 
 # ------------------------------------------------------------------------------ GPU arm
 
+def ri_main(args):
+    """The RI 4-index assembly (eq 14) alone, on seeded synthetic matrices of a job's shape: a
+    symmetric positive definite (P|Q) = X X^T / n + I and a normal (P|ij); factor, solve of all
+    pair columns and the first min(m, 4096)^2 block of (ij|kl), FP64 and on the tensor cores."""
+    import torch
+    from paper_2510_15204_gb300 import build as B
+    B.build()
+    n, m = (int(x) for x in args.ri_sizes.split(","))
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(args.seed)
+    X = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    J2 = X @ X.T / n + torch.eye(n, dtype=torch.float64, device="cuda")
+    J3 = torch.randn((n, m), dtype=torch.float64, device="cuda", generator=g)
+    stream = torch.cuda.Stream()
+    res = time_ri(J2, J3, stream)
+    print(json.dumps({"metric": "RI 4-index assembly (eq 14), synthetic matrices", "unit": "ms", "n_aux": n,
+                      "pairs": m, "ri_4index": res, "data": "synthetic", "seed": args.seed}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.ri_sizes:
+        return ri_main(args)
     if args.serve:
         return serve_main(args)
     if args.scan:
