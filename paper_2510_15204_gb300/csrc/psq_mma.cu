@@ -333,7 +333,8 @@ constexpr int kM = kMmaM;
 constexpr int kTileN = kMmaN;
 constexpr int kChunk = kChunkPts;
 constexpr int kRowB = 2 * kChunkPts;            // bytes of one operand row of a stage (64)
-constexpr int kStages = 3;                      // shared-memory ring depth (chunks)
+constexpr int kStages = 3;                      // A ring depth (chunks, 40 KB each)
+constexpr int kStagesB = 3;                     // B ring depth (chunks, 15 KB each)
 constexpr int kChunksPerWin = kWinPts / kChunkPts;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -448,34 +449,45 @@ namespace mma {
 // (|lo| <= 2^-24 |hi|; s3 <= 256); JOIN = 1 for products left unnormalised (|lo| <= 3 2^-24
 // |hi|: the join adds at most 1.5 to s2, which stays <= 130, and rounds at 2^-17 of s2's unit,
 // 2^-40 of the window's largest value).
-// Nearest integer (ties to even) of |x| < 2^22 by the FP32 magic number 1.5 * 2^23: x + M lies
-// in [2^23, 2^24), where the spacing is 1, so the addition rounds x to an integer and the
-// subtraction is exact (two full-rate adds instead of a conversion-pipe instruction).
-__device__ __forceinline__ float rne_small(float x) { return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f); }
+//
+// Each digit takes three full-rate FP32 instructions.  With M = 1.5 x 2^23 and |x| < 2^22,
+// t = x + M rounds x to its nearest integer s (ties to even): t lies in [2^23, 2^24), where the
+// spacing is 1, so t = M + s exactly.  Then fma(t, -256, 256 M) = -256 s and
+// fma(x, 256, -256 s) = 256 (x - s) are exact (|x - s| <= 1/2 is a multiple of x's spacing).
+// The stored digit is -256 s, exact in BF16 like s (at most 8 significant bits); every operand
+// is stored this way, so a slice product carries 2^16, which keeps the order sums exact in FP32
+// (multiples of 2^16 below 2^40) and which the fold removes with the window scales.
+constexpr float kRneMagic = 12582912.0f;         // 1.5 x 2^23
+constexpr float kRneMagic256 = 3221225472.0f;    // 256 x 1.5 x 2^23 = 1.5 x 2^31
+constexpr int kDigitScaleExp = 8;                // |stored digit| = 2^8 |s|
 
-// BF16x2 bits of two floats that are exact in BF16 (integers of at most 8 significant bits:
-// their low 16 bits are zero), first value in the low half.
+// BF16x2 bits of two floats that are exact in BF16 (at most 8 significant bits: their low 16
+// bits are zero), first value in the low half.
 __device__ __forceinline__ uint32_t pack_bf16_exact(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
 template <int JOIN>
 __device__ __forceinline__ void slice8_df(const float* vh, const float* vl, float sc, uint4* w) {
-  constexpr float kJoin = JOIN == 2 ? 16777216.0f : 65536.0f;  // 256^JOIN
+  constexpr float kJoin = JOIN == 2 ? 16777216.0f : 65536.0f;  // 256^(JOIN + 1)
   uint32_t o[kSlices][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float r0 = vh[2 * q] * sc, r1 = vh[2 * q + 1] * sc;
-    const float l0 = vl[2 * q] * sc * kJoin, l1 = vl[2 * q + 1] * sc * kJoin;
+    // (lo sc) first: sc reaches 2^117 for the smallest rows, where sc 256^(JOIN + 1) would overflow
+    const float l0 = (vl[2 * q] * sc) * kJoin, l1 = (vl[2 * q + 1] * sc) * kJoin;
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) {
-      const float a0 = rne_small(r0), a1 = rne_small(r1);
-      o[k][q] = pack_bf16_exact(a0, a1);
-      r0 = (r0 - a0) * 256.0f;
-      r1 = (r1 - a1) * 256.0f;
-      if (k == JOIN) {
-        r0 += l0;
-        r1 += l1;
+      const float t0 = __fadd_rn(r0, kRneMagic), t1 = __fadd_rn(r1, kRneMagic);
+      const float d0 = __fmaf_rn(t0, -256.0f, kRneMagic256), d1 = __fmaf_rn(t1, -256.0f, kRneMagic256);
+      o[k][q] = pack_bf16_exact(d0, d1);
+      if (k + 1 < kSlices) {
+        r0 = __fmaf_rn(r0, 256.0f, d0);
+        r1 = __fmaf_rn(r1, 256.0f, d1);
+        if (k == JOIN) {
+          r0 = __fadd_rn(r0, l0);
+          r1 = __fadd_rn(r1, l1);
+        }
       }
     }
   }
@@ -640,22 +652,23 @@ __device__ __forceinline__ void prod_unnorm(float xh, float xl, float yh, float 
 //
 // One persistent CTA per SM, 512 threads, working through tiles (128 A rows x <= 48 B
 // columns x a range of 128-point windows):
-//   warp 4       loader: bulk copies of the packed A tile (and packed B tile) of every 32-point
-//                chunk into a three-stage ring, and of the staged basis rows (hi and lo planes)
-//                of formed B tiles, one copy per row, plane and window;
+//   warp 4       loader: bulk copies of the packed A tile of every 32-point chunk into a
+//                three-stage A ring and, for a packed B, of its B tile into a three-stage B
+//                ring (the rings have separate barriers and may differ in depth);
 //   warps 0-3, 6, 7  producers: for a formed B, column c of the tile = product of two staged
 //                rows (a double-float product); each warp owns 8 columns, four lanes per
-//                column, lane g the 16-byte group g of every chunk; per window they find each
-//                column's scale, then slice chunk by chunk into the B stages, so that the MMAs
-//                of one chunk overlap the slicing of the next (for a packed B they only pass
-//                each chunk on);
+//                column, lane g the 16-byte group g of every chunk; per window they form the
+//                products, find each column's scale, then slice chunk by chunk into the B ring,
+//                so that the MMAs of one chunk overlap the slicing of the next (for a packed B
+//                they only pass each chunk on).  Producer warp 0 requests the staged basis rows
+//                (hi and lo planes) of the next formed window while this one is sliced;
 //   warp 5       MMA issue: per chunk 2 K-steps x 5 MMAs (A plane i against B planes
 //                0..4-i, contiguous in shared memory: one MMA of N = 48 (5 - i) whose columns
 //                land on the order accumulators i..4) into the window's TMEM accumulator set
 //                (5 orders x 48 columns; two sets);
 //   warps 8-15   fold: per window, the five order sums of their TMEM lane quadrant and column
 //                half, scaled by the window's row and column exponents, into double-float
-//                registers (orders 0, 1 and 2 join the sum exactly through TwoSums, orders 3-4
+//                registers (orders 0 and 1 join the sum exactly through TwoSums, orders 2-4
 //                as one FP32 term); at the end of the tile, (hi, lo) partials to global memory.
 // Every wait is bounded (wait_ns in the main loops, the fixed kWaitNs for the drains); a
 // timeout sets *status and the CTA's abort flag, and each role leaves its loops at its next
@@ -670,11 +683,11 @@ constexpr int kRawStride = 132;  // floats per staged row: 128 points + 4 (bank 
 
 struct Smem {
   alignas(1024) uint8_t a[mma::kStages][kSlices][mma::kM * mma::kRowB];
-  alignas(1024) uint8_t b[mma::kStages][kSlices][mma::kTileN * mma::kRowB];
+  alignas(1024) uint8_t b[mma::kStagesB][kSlices][mma::kTileN * mma::kRowB];
   alignas(16) float raw[2][2][kPairTileRows][kRawStride];  // [buffer][hi, lo][row][point]
   int eb[2][mma::kTileN];
   float sbw[8][mma::kTileN];  // fold warp k: the column scales of the current window
-  alignas(8) uint64_t a_full[mma::kStages], b_ready[mma::kStages], stage_free[mma::kStages];
+  alignas(8) uint64_t a_full[mma::kStages], a_free[mma::kStages], b_ready[mma::kStagesB], b_free[mma::kStagesB];
   uint64_t tmem_full[2], tmem_free[2], raw_full[2], raw_free[2], eb_free[2];
   uint64_t drain;
   uint32_t tmem_base;
@@ -710,9 +723,21 @@ __device__ __forceinline__ bool wait(uint64_t* b, uint32_t parity, const int* ab
   return mma::mbar_wait(mma::smem_u32(b), parity, abort, limit_ns);
 }
 
-// Ring position of chunk c: stage c % kStages, completed rounds c / kStages.
+// Ring positions of chunk c: A stage c % kStages after c / kStages completed rounds, B stage
+// c % kStagesB after c / kStagesB rounds.
 __device__ __forceinline__ int stage_of(uint32_t c) { return (int)(c % mma::kStages); }
 __device__ __forceinline__ uint32_t round_of(uint32_t c) { return c / mma::kStages; }
+__device__ __forceinline__ int bstage_of(uint32_t c) { return (int)(c % mma::kStagesB); }
+__device__ __forceinline__ uint32_t bround_of(uint32_t c) { return c / mma::kStagesB; }
+// A stage of chunk c free again (its MMAs of chunk c - kStages complete)
+__device__ __forceinline__ bool wait_a_free(Smem& sm, uint32_t c, uint64_t ns) {
+  return c < (uint32_t)mma::kStages || mma::mbar_wait(mma::smem_u32(&sm.a_free[stage_of(c)]), (round_of(c) - 1) & 1, &sm.abort, ns);
+}
+// B stage of chunk c free again (its MMAs of chunk c - kStagesB complete)
+__device__ __forceinline__ bool wait_b_free(Smem& sm, uint32_t c, uint64_t ns) {
+  return c < (uint32_t)mma::kStagesB ||
+         mma::mbar_wait(mma::smem_u32(&sm.b_free[bstage_of(c)]), (bround_of(c) - 1) & 1, &sm.abort, ns);
+}
 
 // What every role needs to know about an item.
 struct Geo {
@@ -749,6 +774,36 @@ __device__ __forceinline__ void fail(Smem& sm, int* status, int code) {
 
 __device__ __forceinline__ bool aborted(Smem& sm) { return *(volatile int*)&sm.abort != 0; }
 
+// Moves (ii, win) to the first window at or after window `win` of item ii that belongs to an
+// item with a formed B (items [ii, ie)); win < 0 means the item's first window.  False when
+// there is none.
+__device__ __forceinline__ bool seek_formed(int& ii, int& win, int ie, const GemmItem* items, const MmaBlock* blocks,
+                                            const DevGrid* grids, const PairTile* ptiles) {
+  for (; ii < ie; ++ii, win = -1) {
+    const Geo q = geo(items[ii], blocks, grids, ptiles);
+    if (!q.formed) continue;
+    if (win < q.w0) win = q.w0;
+    if (win < q.w1) return true;
+  }
+  return false;
+}
+
+// Bulk copies of the staged basis rows (hi and lo planes, 512 bytes per row and plane) of
+// window `win` of formed item `it` into raw buffer rb, completing on raw_full[rb]; one warp.
+__device__ __forceinline__ void request_rows(Smem& sm, int rb, const GemmItem& it, int win, const MmaBlock* blocks,
+                                             const DevGrid* grids, const PairTile* ptiles, const float* ops,
+                                             const float* ops_lo, int lane) {
+  const Geo q = geo(it, blocks, grids, ptiles);
+  const DevGrid& g = grids[q.blk->grid];
+  const int nr = q.pt->nrows;  // <= kPairTileRows (16): lanes 0-15 hi, 16-31 lo
+  if (lane == 0) mbar_expect_tx(&sm.raw_full[rb], (uint32_t)nr * 2u * 512u);
+  __syncwarp();
+  const int rr = lane & 15, pl = lane >> 4;
+  if (rr < nr)
+    bulk_g2s(sm.raw[rb][pl][rr], (pl ? ops_lo : ops) + g.op_off + (int64_t)q.pt->rows[rr] * g.ld + (int64_t)kWinPts * win,
+             512u, &sm.raw_full[rb]);
+}
+
 }  // namespace ws
 
 __global__ void __launch_bounds__(ws::kThreads, 1)
@@ -770,8 +825,11 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
       ws::mbar_init(&sm.a_full[s], 1);
+      ws::mbar_init(&sm.a_free[s], 1);
+    }
+    for (int s = 0; s < kStagesB; ++s) {
       ws::mbar_init(&sm.b_ready[s], 6);
-      ws::mbar_init(&sm.stage_free[s], 1);
+      ws::mbar_init(&sm.b_free[s], 1);
     }
     for (int s = 0; s < 2; ++s) {
       ws::mbar_init(&sm.tmem_full[s], 1);
@@ -793,8 +851,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
   constexpr unsigned kFull = 0xffffffffu;
   if (warp == ws::kLoadWarp) {
     // ------------------------------------------------------------------ loader
-    bool run = true;                 // warp-uniform
-    int last_a = -1, last_raw = -1;  // last issued chunk / formed window (for the drain)
+    bool run = true;  // warp-uniform
+    int last_a = -1;  // last issued chunk (for the drain)
     if (hold) {
       // failure-detection test: a raised flag that nothing clears holds the first copy back
       // until the wait limit runs out
@@ -813,31 +871,13 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
       const MmaBlock& b = *q.blk;
-      const DevGrid& g = grids[b.grid];
       const Panel& pa = panels[b.a_panel];
       const Panel* pb = q.formed ? nullptr : panels + b.b_panel;
       for (int win = q.w0; win < q.w1 && run; ++win, ++w) {
         const int nck = ws::chunks_in(q, win);
-        if (q.formed) {
-          const int rb = rw & 1;
-          const bool ok = rw < 2 || ws::wait(&sm.raw_free[rb], ((rw - 2) >> 1) & 1, &sm.abort, wait_ns);
-          run = __all_sync(kFull, ok && !ws::aborted(sm));
-          if (!run) { ws::fail(sm, status, 4); break; }
-          const int nr = q.pt->nrows;  // <= kPairTileRows (16): lanes 0-15 hi, 16-31 lo
-          if (lane == 0) ws::mbar_expect_tx(&sm.raw_full[rb], (uint32_t)nr * 2u * 512u);
-          __syncwarp();
-          const int rr = lane & 15, pl = lane >> 4;
-          if (rr < nr)
-            ws::bulk_g2s(sm.raw[rb][pl][rr],
-                         (pl ? ops_lo : ops) + g.op_off + (int64_t)q.pt->rows[rr] * g.ld + (int64_t)kWinPts * win,
-                         512u, &sm.raw_full[rb]);
-          last_raw = (int)rw;
-          ++rw;
-        }
         for (int j = 0; j < nck; ++j, ++c) {
-          const int s = ws::stage_of(c), ch = kChunksPerWin * win + j;
-          const bool ok = c < (uint32_t)kStages ||
-                          ws::wait(&sm.stage_free[s], (ws::round_of(c) - 1) & 1, &sm.abort, wait_ns);
+          const int s = ws::stage_of(c), sb = ws::bstage_of(c), ch = kChunksPerWin * win + j;
+          const bool ok = ws::wait_a_free(sm, c, wait_ns) && (!pb || ws::wait_b_free(sm, c, wait_ns));
           run = __all_sync(kFull, ok && !ws::aborted(sm));
           if (!run) { ws::fail(sm, status, 4); break; }
           // the stored rows of the tiles, one bulk copy per plane (lanes 0-4: A, 5-9: B)
@@ -853,7 +893,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
             const int k = lane - kSlices;
             const uint8_t* src = packed + pb->pack_off + (int64_t)it.tn * pb->nch * (kSlices * kTileN * kRowB) +
                                  (int64_t)ch * (kSlices * rbw * kRowB) + (int64_t)k * rbw * kRowB;
-            ws::bulk_g2s(sm.b[s][k], src, (uint32_t)(kRowB * rbw), &sm.a_full[s]);
+            ws::bulk_g2s(sm.b[sb][k], src, (uint32_t)(kRowB * rbw), &sm.a_full[s]);
           }
           __syncwarp();
           last_a = (int)c;
@@ -865,8 +905,6 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     // ones issued on each barrier, complete at once when the copies were consumed)
     for (int k = last_a; k >= 0 && k > last_a - kStages; --k)
       ws::wait(&sm.a_full[ws::stage_of(k)], ws::round_of(k) & 1, nullptr, kWaitNs);
-    for (int k = last_raw; k >= 0 && k > last_raw - 2; --k)
-      ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1, nullptr, kWaitNs);
   } else if (warp < 4 || warp == 6 || warp == 7) {
     // ------------------------------------------------------------------ producers
     const int pw = warp < 4 ? warp : warp - 2;  // 0..5
@@ -874,7 +912,27 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const int g = lane & 3;                     // 16-byte group of each chunk's row
     const unsigned col_mask = 0xfu << (lane & 28);
     bool run = true;  // warp-uniform
-    for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
+    // Warp 0 requests the staged rows of the formed windows, in the order they are sliced
+    // (across items), one window ahead: window rw + 1's rows are copied while window rw is
+    // sliced.  (ri, rwin) is the next formed window to request, rq the windows requested.
+    const int i_end = cta_begin[blockIdx.x + 1];
+    int ri = cta_begin[blockIdx.x], rwin = -1;
+    bool more = pw == 0 && ws::seek_formed(ri, rwin, i_end, items, blocks, grids, ptiles);
+    uint32_t rq = 0;
+    auto request = [&](uint32_t upto) -> bool {  // requests windows [rq, upto); false on failure
+      while (more && rq < upto) {
+        const int rb = (int)(rq & 1);
+        // buffer rb last held formed window rq - 2, which every producer has released
+        const bool ok = rq < 2 || ws::wait(&sm.raw_free[rb], ((rq - 2) >> 1) & 1, &sm.abort, wait_ns);
+        if (!__all_sync(kFull, ok && !ws::aborted(sm))) return false;
+        ws::request_rows(sm, rb, items[ri], rwin, blocks, grids, ptiles, ops, ops_lo, lane);
+        ++rq;
+        ++rwin;
+        more = ws::seek_formed(ri, rwin, i_end, items, blocks, grids, ptiles);
+      }
+      return true;
+    };
+    for (int ii = cta_begin[blockIdx.x], ie = i_end; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
       if (!q.formed) {
@@ -882,12 +940,11 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         for (int win = q.w0; win < q.w1 && run; ++win, ++w) {
           const int nck = ws::chunks_in(q, win);
           for (int j = 0; j < nck; ++j, ++c) {
-            const int s = ws::stage_of(c);
-            const bool ok = c < (uint32_t)kStages ||
-                            ws::wait(&sm.stage_free[s], (ws::round_of(c) - 1) & 1, &sm.abort, wait_ns);
+            const int sb = ws::bstage_of(c);
+            const bool ok = ws::wait_b_free(sm, c, wait_ns);
             run = __all_sync(kFull, ok && !ws::aborted(sm));
             if (!run) { ws::fail(sm, status, 5); break; }
-            if (lane == 0) ws::mbar_arrive(&sm.b_ready[s]);
+            if (lane == 0) ws::mbar_arrive(&sm.b_ready[sb]);
           }
         }
         continue;
@@ -897,6 +954,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       for (int win = q.w0; win < q.w1 && run; ++win, ++w, ++rw) {
         const int nck = ws::chunks_in(q, win);
         const int rb = rw & 1, set = w & 1;
+        if (pw == 0 && !request(rw + 1)) { run = false; ws::fail(sm, status, 5); break; }  // the first window
         bool ok = ws::wait(&sm.raw_full[rb], (rw >> 1) & 1, &sm.abort, wait_ns);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 5); break; }
@@ -934,6 +992,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(vh[cc][i]));
         }
+        // the next formed window's rows, into the buffer that window rw - 1 used
+        if (pw == 0 && !request(rw + 2)) { run = false; ws::fail(sm, status, 5); break; }
         // the column's window maximum over its four lanes
         mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 1));
         mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 2));
@@ -948,9 +1008,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
         for (int cc = 0; cc < kChunksPerWin; ++cc) {
           if (cc < nck && run) {
-            const int s = ws::stage_of(c);
-            const bool okc = c < (uint32_t)kStages ||
-                             ws::wait(&sm.stage_free[s], (ws::round_of(c) - 1) & 1, &sm.abort, wait_ns);
+            const int sb = ws::bstage_of(c);
+            const bool okc = ws::wait_b_free(sm, c, wait_ns);
             run = __all_sync(kFull, okc && !ws::aborted(sm));
             if (!run) {
               ws::fail(sm, status, 5);
@@ -958,10 +1017,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
               uint4 wv[kSlices];
               slice8_df<1>(vh[cc], vl[cc], sc, wv);
 #pragma unroll
-              for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(sm.b[s][k] + swz(col, g)) = wv[k];
+              for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(sm.b[sb][k] + swz(col, g)) = wv[k];
               fence_async_smem();
               __syncwarp();
-              if (lane == 0) ws::mbar_arrive(&sm.b_ready[s]);
+              if (lane == 0) ws::mbar_arrive(&sm.b_ready[sb]);
               ++c;
             }
           }
@@ -971,6 +1030,10 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         if (lane == 0) ws::mbar_arrive(&sm.raw_free[rb]);
       }
     }
+    // drain: rows requested but not consumed (a role gave up) must land before the CTA exits;
+    // a window whose copy was already waited for completes at once
+    if (pw == 0)
+      for (uint32_t k = rw; k < rq; ++k) ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1, nullptr, kWaitNs);
   } else if (warp == ws::kMmaWarp) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
@@ -984,10 +1047,9 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
           if (w >= 2) ok = ws::wait(&sm.tmem_free[set], ((w - 2) >> 1) & 1, &sm.abort, wait_ns);
           const uint32_t tset = tmem + (uint32_t)set * 256u;
           for (int j = 0; j < nck && ok; ++j, ++c) {
-            const int s = ws::stage_of(c);
-            const uint32_t par = ws::round_of(c) & 1;
-            ok = ws::wait(&sm.a_full[s], par, &sm.abort, wait_ns);
-            if (ok) ok = ws::wait(&sm.b_ready[s], par, &sm.abort, wait_ns);
+            const int s = ws::stage_of(c), sb = ws::bstage_of(c);
+            ok = ws::wait(&sm.a_full[s], ws::round_of(c) & 1, &sm.abort, wait_ns);
+            if (ok) ok = ws::wait(&sm.b_ready[sb], ws::bround_of(c) & 1, &sm.abort, wait_ns);
             if (!ok) break;
             fence_after();
             // The B planes of a stage are contiguous (48 rows each), so plane i of A against
@@ -996,7 +1058,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
             for (int k = 0; k < kChunk / 16; ++k) {
               const uint32_t ko = 32u * k;
-              const uint64_t db = make_desc(smem_u32(sm.b[s][0]) + ko);
+              const uint64_t db = make_desc(smem_u32(sm.b[sb][0]) + ko);
 #pragma unroll
               for (int i = 0; i < kSlices; ++i) {
                 const uint64_t da = make_desc(smem_u32(sm.a[s][i]) + ko);
@@ -1004,7 +1066,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
                          (j > 0 || k > 0 || i > 0) ? 1u : 0u);
               }
             }
-            mma_commit(smem_u32(&sm.stage_free[s]));
+            mma_commit(smem_u32(&sm.a_free[s]));
+            mma_commit(smem_u32(&sm.b_free[sb]));
           }
           if (!ok) { ws::fail(sm, status, 6); break; }
           mma_commit(smem_u32(&sm.tmem_full[set]));
@@ -1054,10 +1117,11 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 7); break; }
         fence_after();
-        // column scales 2^(e_b - 7) for this warp, row scale 2^(e_a - 7) for this thread
+        // column scales 2^(e_b - 7 - 8) for this warp, row scale 2^(e_a - 7 - 8) for this
+        // thread (each stored digit carries 2^8)
         float* sbw = sm.sbw[ew];
-        if (lane < 24) sbw[my_col] = pow2f((pb ? eb_lane : sm.eb[set][my_col]) - 7);
-        const float sa = pow2f(ea - 7);
+        if (lane < 24) sbw[my_col] = pow2f((pb ? eb_lane : sm.eb[set][my_col]) - 7 - kDigitScaleExp);
+        const float sa = pow2f(ea - 7 - kDigitScaleExp);
         __syncwarp();
         if (lane == 0) ws::mbar_arrive(&sm.eb_free[set]);  // the producers may refill eb[set]
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)set * 256u;
@@ -1074,7 +1138,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
                 const int qq = 8 * gi + j;
-                const float sc = sa * sbw[c0 + j];  // 2^(e_a + e_b - 14)
+                const float sc = sa * sbw[c0 + j];  // 2^(e_a + e_b - 30)
                 // orders 0 and 1 (exact integers times powers of two) into the double-float sum
                 // through TwoSums; orders 2-4, at most 2^-15 of order 0, as one FP32 term into
                 // the lo word (rounded at 2^-39 of the window's largest)
@@ -1187,6 +1251,8 @@ cudaError_t launch_eval_mixed(const LaunchTables& t, const NodeEntry* tab, const
   return cudaGetLastError();
 }
 
+// the ring, staging buffers and barriers, plus 1 KB to align the ring's start
+static_assert(sizeof(ws::Smem) + 1024 <= 232448, "contraction shared memory above the 227 KB a CTA may use");
 size_t ws_smem_bytes() { return sizeof(ws::Smem) + 1024; }
 
 cudaError_t prepare_kernels() {
