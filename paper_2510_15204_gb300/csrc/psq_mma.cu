@@ -382,6 +382,19 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   return done != 0;
 }
 
+// Non-blocking test of the phase of the given parity.
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -652,16 +665,16 @@ __device__ __forceinline__ void prod_unnorm(float xh, float xl, float yh, float 
 //
 // One persistent CTA per SM, 512 threads, working through tiles (128 A rows x <= 48 B
 // columns x a range of 128-point windows):
-//   warp 4       loader: bulk copies of the packed A tile of every 32-point chunk into a
-//                three-stage A ring and, for a packed B, of its B tile into a three-stage B
-//                ring (the rings have separate barriers and may differ in depth);
+//   warp 4       loader: two ordered streams of bulk copies, each served as soon as its next
+//                buffer is free: the packed A tile of every 32-point chunk into a three-stage
+//                A ring (and, for a packed B, its B tile into the B ring), and the staged basis
+//                rows (hi and lo planes) of every formed window into two buffers;
 //   warps 0-3, 6, 7  producers: for a formed B, column c of the tile = product of two staged
 //                rows (a double-float product); each warp owns 8 columns, four lanes per
 //                column, lane g the 16-byte group g of every chunk; per window they form the
 //                products, find each column's scale, then slice chunk by chunk into the B ring,
 //                so that the MMAs of one chunk overlap the slicing of the next (for a packed B
-//                they only pass each chunk on).  Producer warp 0 requests the staged basis rows
-//                (hi and lo planes) of the next formed window while this one is sliced;
+//                they only pass each chunk on);
 //   warp 5       MMA issue: per chunk 2 K-steps x 5 MMAs (A plane i against B planes
 //                0..4-i, contiguous in shared memory: one MMA of N = 48 (5 - i) whose columns
 //                land on the order accumulators i..4) into the window's TMEM accumulator set
@@ -774,35 +787,50 @@ __device__ __forceinline__ void fail(Smem& sm, int* status, int code) {
 
 __device__ __forceinline__ bool aborted(Smem& sm) { return *(volatile int*)&sm.abort != 0; }
 
-// Moves (ii, win) to the first window at or after window `win` of item ii that belongs to an
-// item with a formed B (items [ii, ie)); win < 0 means the item's first window.  False when
-// there is none.
-__device__ __forceinline__ bool seek_formed(int& ii, int& win, int ie, const GemmItem* items, const MmaBlock* blocks,
-                                            const DevGrid* grids, const PairTile* ptiles) {
-  for (; ii < ie; ++ii, win = -1) {
-    const Geo q = geo(items[ii], blocks, grids, ptiles);
-    if (!q.formed) continue;
-    if (win < q.w0) win = q.w0;
-    if (win < q.w1) return true;
-  }
-  return false;
-}
+// The loader's stream of staged-row requests: the formed windows of the CTA's items in the
+// order the producers form them, with the current item's tile rows and grid offsets cached
+// (one lookup per item, not per window).
+struct RowStream {
+  int ii, ie, win, w1;  // current item, end, next window, the item's window end
+  int nr;               // staged rows of the item's pair tile (<= kPairTileRows)
+  int64_t src;          // this lane's row (lane & 15) of plane (lane >> 4), window 0, in floats
+  bool more;
 
-// Bulk copies of the staged basis rows (hi and lo planes, 512 bytes per row and plane) of
-// window `win` of formed item `it` into raw buffer rb, completing on raw_full[rb]; one warp.
-__device__ __forceinline__ void request_rows(Smem& sm, int rb, const GemmItem& it, int win, const MmaBlock* blocks,
-                                             const DevGrid* grids, const PairTile* ptiles, const float* ops,
-                                             const float* ops_lo, int lane) {
-  const Geo q = geo(it, blocks, grids, ptiles);
-  const DevGrid& g = grids[q.blk->grid];
-  const int nr = q.pt->nrows;  // <= kPairTileRows (16): lanes 0-15 hi, 16-31 lo
-  if (lane == 0) mbar_expect_tx(&sm.raw_full[rb], (uint32_t)nr * 2u * 512u);
-  __syncwarp();
-  const int rr = lane & 15, pl = lane >> 4;
-  if (rr < nr)
-    bulk_g2s(sm.raw[rb][pl][rr], (pl ? ops_lo : ops) + g.op_off + (int64_t)q.pt->rows[rr] * g.ld + (int64_t)kWinPts * win,
-             512u, &sm.raw_full[rb]);
-}
+  __device__ __forceinline__ void open(int i0, int i1, const GemmItem* items, const MmaBlock* blocks,
+                                       const DevGrid* grids, const PairTile* ptiles, int lane) {
+    ii = i0;
+    ie = i1;
+    win = -1;
+    more = false;
+    seek(items, blocks, grids, ptiles, lane, false);
+  }
+  // Advances to the next formed window (the next window of the current item when `step`).
+  __device__ __forceinline__ void seek(const GemmItem* items, const MmaBlock* blocks, const DevGrid* grids,
+                                       const PairTile* ptiles, int lane, bool step) {
+    if (step && ++win < w1) return;
+    if (step) ++ii;
+    for (; ii < ie; ++ii) {
+      const Geo q = geo(items[ii], blocks, grids, ptiles);
+      if (!q.formed) continue;
+      const DevGrid& g = grids[q.blk->grid];
+      win = q.w0;
+      w1 = q.w1;
+      nr = q.pt->nrows;
+      src = g.op_off + (int64_t)q.pt->rows[max(0, min(lane & 15, nr - 1))] * g.ld;
+      more = win < w1;
+      if (more) return;
+    }
+    more = false;
+  }
+  // Bulk copies of the current window's rows (hi and lo planes, 512 bytes per row and plane)
+  // into raw buffer rb, completing on raw_full[rb]; one warp.
+  __device__ __forceinline__ void request(Smem& sm, int rb, const float* ops, const float* ops_lo, int lane) const {
+    if (lane == 0) mbar_expect_tx(&sm.raw_full[rb], (uint32_t)nr * 2u * 512u);
+    __syncwarp();
+    const int rr = lane & 15, pl = lane >> 4;
+    if (rr < nr) bulk_g2s(sm.raw[rb][pl][rr], (pl ? ops_lo : ops) + src + (int64_t)kWinPts * win, 512u, &sm.raw_full[rb]);
+  }
+};
 
 }  // namespace ws
 
@@ -867,15 +895,37 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         run = false;
       }
     }
-    for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
+    // Two ordered streams: the packed A (and packed B) tiles of every chunk into the rings, and
+    // the staged basis rows of every formed window into two buffers (the rows of formed window
+    // k + 1 are in flight while the producers form window k).  The warp waits for the chunk
+    // stream's buffers and, before each of those waits, requests every window of rows whose
+    // buffer is already free.
+    const int ie = cta_begin[blockIdx.x + 1];
+    ws::RowStream rs;
+    rs.open(cta_begin[blockIdx.x], ie, items, blocks, grids, ptiles, lane);
+    uint32_t rq = 0;  // formed windows requested
+    auto request_free = [&]() {
+      while (rs.more) {
+        // buffer rq & 1 last held formed window rq - 2, released after its products
+        const int rb = (int)(rq & 1);
+        int free_ = 1;
+        if (lane == 0) free_ = rq < 2 || mbar_test(smem_u32(&sm.raw_free[rb]), ((rq - 2) >> 1) & 1);
+        if (!__shfl_sync(kFull, free_, 0)) return;
+        rs.request(sm, rb, ops, ops_lo, lane);
+        ++rq;
+        rs.seek(items, blocks, grids, ptiles, lane, true);
+      }
+    };
+    for (int ii = cta_begin[blockIdx.x]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
       const MmaBlock& b = *q.blk;
       const Panel& pa = panels[b.a_panel];
       const Panel* pb = q.formed ? nullptr : panels + b.b_panel;
-      for (int win = q.w0; win < q.w1 && run; ++win, ++w) {
+      for (int win = q.w0; win < q.w1 && run; ++win) {
         const int nck = ws::chunks_in(q, win);
         for (int j = 0; j < nck; ++j, ++c) {
+          request_free();
           const int s = ws::stage_of(c), sb = ws::bstage_of(c), ch = kChunksPerWin * win + j;
           const bool ok = ws::wait_a_free(sm, c, wait_ns) && (!pb || ws::wait_b_free(sm, c, wait_ns));
           run = __all_sync(kFull, ok && !ws::aborted(sm));
@@ -900,11 +950,21 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         }
       }
     }
+    // the rows of the last formed windows, as their buffers free up
+    while (run && rs.more) {
+      const int rb = (int)(rq & 1);
+      const bool ok = rq < 2 || ws::wait(&sm.raw_free[rb], ((rq - 2) >> 1) & 1, &sm.abort, wait_ns);
+      run = __all_sync(kFull, ok && !ws::aborted(sm));
+      if (!run) { ws::fail(sm, status, 4); break; }
+      request_free();
+    }
     // drain: nothing may still be copying into shared memory when the CTA exits (another
     // role may have given up after this loop ended; the phases waited for here are the last
     // ones issued on each barrier, complete at once when the copies were consumed)
     for (int k = last_a; k >= 0 && k > last_a - kStages; --k)
       ws::wait(&sm.a_full[ws::stage_of(k)], ws::round_of(k) & 1, nullptr, kWaitNs);
+    for (int k = (int)rq - 1; k >= 0 && k > (int)rq - 3; --k)
+      ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1, nullptr, kWaitNs);
   } else if (warp < 4 || warp == 6 || warp == 7) {
     // ------------------------------------------------------------------ producers
     const int pw = warp < 4 ? warp : warp - 2;  // 0..5
@@ -912,27 +972,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
     const int g = lane & 3;                     // 16-byte group of each chunk's row
     const unsigned col_mask = 0xfu << (lane & 28);
     bool run = true;  // warp-uniform
-    // Warp 0 requests the staged rows of the formed windows, in the order they are sliced
-    // (across items), one window ahead: window rw + 1's rows are copied while window rw is
-    // sliced.  (ri, rwin) is the next formed window to request, rq the windows requested.
-    const int i_end = cta_begin[blockIdx.x + 1];
-    int ri = cta_begin[blockIdx.x], rwin = -1;
-    bool more = pw == 0 && ws::seek_formed(ri, rwin, i_end, items, blocks, grids, ptiles);
-    uint32_t rq = 0;
-    auto request = [&](uint32_t upto) -> bool {  // requests windows [rq, upto); false on failure
-      while (more && rq < upto) {
-        const int rb = (int)(rq & 1);
-        // buffer rb last held formed window rq - 2, which every producer has released
-        const bool ok = rq < 2 || ws::wait(&sm.raw_free[rb], ((rq - 2) >> 1) & 1, &sm.abort, wait_ns);
-        if (!__all_sync(kFull, ok && !ws::aborted(sm))) return false;
-        ws::request_rows(sm, rb, items[ri], rwin, blocks, grids, ptiles, ops, ops_lo, lane);
-        ++rq;
-        ++rwin;
-        more = ws::seek_formed(ri, rwin, i_end, items, blocks, grids, ptiles);
-      }
-      return true;
-    };
-    for (int ii = cta_begin[blockIdx.x], ie = i_end; ii < ie && run; ++ii) {
+    for (int ii = cta_begin[blockIdx.x], ie = cta_begin[blockIdx.x + 1]; ii < ie && run; ++ii) {
       const GemmItem it = items[ii];
       const ws::Geo q = ws::geo(it, blocks, grids, ptiles);
       if (!q.formed) {
@@ -954,7 +994,6 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
       for (int win = q.w0; win < q.w1 && run; ++win, ++w, ++rw) {
         const int nck = ws::chunks_in(q, win);
         const int rb = rw & 1, set = w & 1;
-        if (pw == 0 && !request(rw + 1)) { run = false; ws::fail(sm, status, 5); break; }  // the first window
         bool ok = ws::wait(&sm.raw_full[rb], (rw >> 1) & 1, &sm.abort, wait_ns);
         run = __all_sync(kFull, ok && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 5); break; }
@@ -992,8 +1031,9 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(vh[cc][i]));
         }
-        // the next formed window's rows, into the buffer that window rw - 1 used
-        if (pw == 0 && !request(rw + 2)) { run = false; ws::fail(sm, status, 5); break; }
+        // the staged rows are read: release the buffer for the window after next
+        __syncwarp();
+        if (lane == 0) ws::mbar_arrive(&sm.raw_free[rb]);
         // the column's window maximum over its four lanes
         mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 1));
         mx = fmaxf(mx, __shfl_xor_sync(col_mask, mx, 2));
@@ -1026,14 +1066,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
           }
         }
         if (!run) break;
-        __syncwarp();
-        if (lane == 0) ws::mbar_arrive(&sm.raw_free[rb]);
       }
     }
-    // drain: rows requested but not consumed (a role gave up) must land before the CTA exits;
-    // a window whose copy was already waited for completes at once
-    if (pw == 0)
-      for (uint32_t k = rw; k < rq; ++k) ws::wait(&sm.raw_full[k & 1], (k >> 1) & 1, nullptr, kWaitNs);
   } else if (warp == ws::kMmaWarp) {
     // ------------------------------------------------------------------ MMA issue
     if (lane == 0) {
