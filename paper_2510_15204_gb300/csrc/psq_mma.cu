@@ -480,15 +480,22 @@ __device__ __forceinline__ uint32_t pack_bf16_exact(float lo, float hi) {
   return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
 
+// The window scale of a row whose largest |value| is below 2^e, for the hi words (sc) and
+// for the lo words joining after digit JOIN (sc 256^(JOIN + 1), capped at 2^127: rows below
+// 2^-96, whose lo parts are below 2^-120, join them at a smaller weight).
 template <int JOIN>
-__device__ __forceinline__ void slice8_df(const float* vh, const float* vl, float sc, uint4* w) {
-  constexpr float kJoin = JOIN == 2 ? 16777216.0f : 65536.0f;  // 256^(JOIN + 1)
+__device__ __forceinline__ void window_scales(int e, float& sc, float& scj) {
+  sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
+  scj = e == kZeroExp ? 0.0f : pow2f(7 - e + 8 * (JOIN + 1));
+}
+
+template <int JOIN>
+__device__ __forceinline__ void slice8_df(const float* vh, const float* vl, float sc, float scj, uint4* w) {
   uint32_t o[kSlices][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     float r0 = vh[2 * q] * sc, r1 = vh[2 * q + 1] * sc;
-    // (lo sc) first: sc reaches 2^117 for the smallest rows, where sc 256^(JOIN + 1) would overflow
-    const float l0 = (vl[2 * q] * sc) * kJoin, l1 = (vl[2 * q + 1] * sc) * kJoin;
+    const float l0 = vl[2 * q] * scj, l1 = vl[2 * q + 1] * scj;
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) {
       const float t0 = __fadd_rn(r0, kRneMagic), t1 = __fadd_rn(r1, kRneMagic);
@@ -564,14 +571,15 @@ __device__ __forceinline__ void pack_store(const PackPos& P, const Panel& pn, co
   const int rt = min(pn.tr, pn.nrows - P.t * pn.tr);
   const int c = kChunksPerWin * P.w + (P.qq >> 1);
   if (c >= pn.nch || P.r >= rt) return;
-  const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
+  float sc, scj;
+  window_scales<2>(e, sc, scj);
   uint8_t* dst = packed + pn.pack_off + (int64_t)P.t * pn.nch * (kSlices * pn.tr * kRowB) +
                  (int64_t)c * (kSlices * rt * kRowB);
   const int plane = rt * kRowB;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     uint4 wv[kSlices];
-    slice8_df<2>(h + 8 * j, l + 8 * j, sc, wv);
+    slice8_df<2>(h + 8 * j, l + 8 * j, sc, scj, wv);
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(P.r, 2 * (P.qq & 1) + j)) = wv[k];
   }
@@ -1044,7 +1052,8 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
         run = __all_sync(kFull, okb && !ws::aborted(sm));
         if (!run) { ws::fail(sm, status, 5); break; }
         if (g == 0) sm.eb[set][col] = e;
-        const float sc = e == kZeroExp ? 0.0f : pow2f(7 - e);
+        float sc, scj;
+        window_scales<1>(e, sc, scj);
 #pragma unroll
         for (int cc = 0; cc < kChunksPerWin; ++cc) {
           if (cc < nck && run) {
@@ -1055,7 +1064,7 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
               ws::fail(sm, status, 5);
             } else {
               uint4 wv[kSlices];
-              slice8_df<1>(vh[cc], vl[cc], sc, wv);
+              slice8_df<1>(vh[cc], vl[cc], sc, scj, wv);
 #pragma unroll
               for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(sm.b[sb][k] + swz(col, g)) = wv[k];
               fence_async_smem();
@@ -1173,15 +1182,21 @@ __global__ void __launch_bounds__(ws::kThreads, 1)
               for (int j = 0; j < 8; ++j) {
                 const int qq = 8 * gi + j;
                 const float sc = sa * sbw[c0 + j];  // 2^(e_a + e_b - 30)
-                // orders 0 and 1 (exact integers times powers of two) into the double-float sum
-                // through TwoSums; orders 2-4, at most 2^-15 of order 0, as one FP32 term into
-                // the lo word (rounded at 2^-39 of the window's largest)
-                const df s0 = dfa::two_sum(H[qq], o[0][j] * sc);
-                const df s1 = dfa::two_sum(s0.h, o[1][j] * (sc * 0.00390625f));
+                // Order 1 splits exactly into q1, its nearest multiple of 2^24 (adding 1.5 x 2^47
+                // rounds at that spacing), and r1 = o1 - q1; q1 / 256 joins order 0 exactly
+                // (both multiples of 2^16 below 2^38).  That part, times the power of two sc,
+                // enters the double-float sum through one TwoSum; r1 / 256 and orders 2-4 (at
+                // most 2^-15 of order 0) join the lo word as one FP32 term, rounded at 2^-16 of
+                // order 0's unit (2^-37 of the window's largest possible sum).
+                const float q1 = __fsub_rn(__fadd_rn(o[1][j], 211106232532992.0f), 211106232532992.0f);
+                const float r1 = __fsub_rn(o[1][j], q1);
+                const df s0 = dfa::two_sum(H[qq], __fmaf_rn(q1, 0.00390625f, o[0][j]) * sc);
                 const float tail =
-                    fmaf(o[2][j], 1.52587890625e-5f, fmaf(o[4][j], 2.3283064365386963e-10f, o[3][j] * 5.9604644775390625e-8f)) * sc;
-                const float lo = L[qq] + ((s0.l + s1.l) + tail);
-                const df r = dfa::fast_two_sum(s1.h, lo);
+                    fmaf(r1, 0.00390625f,
+                         fmaf(o[2][j], 1.52587890625e-5f, fmaf(o[4][j], 2.3283064365386963e-10f, o[3][j] * 5.9604644775390625e-8f))) *
+                    sc;
+                const float lo = L[qq] + (s0.l + tail);
+                const df r = dfa::fast_two_sum(s0.h, lo);
                 H[qq] = r.h;
                 L[qq] = r.l;
               }
