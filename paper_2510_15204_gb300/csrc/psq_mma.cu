@@ -492,18 +492,21 @@ __device__ __forceinline__ void window_scales(int e, float& sc, float& scj) {
 template <int JOIN>
 __device__ __forceinline__ void slice8_df(const float* vh, const float* vl, float sc, float scj, uint4* w) {
   uint32_t o[kSlices][4];
+  const float sc256 = sc * 256.0f;  // at most 2^125
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    float r0 = vh[2 * q] * sc, r1 = vh[2 * q + 1] * sc;
+    float r0 = 0.0f, r1 = 0.0f;
     const float l0 = vl[2 * q] * scj, l1 = vl[2 * q + 1] * scj;
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) {
-      const float t0 = __fadd_rn(r0, kRneMagic), t1 = __fadd_rn(r1, kRneMagic);
+      // digit 0 rounds v sc (exact: sc is a power of two) inside its first FMA
+      const float t0 = k == 0 ? __fmaf_rn(vh[2 * q], sc, kRneMagic) : __fadd_rn(r0, kRneMagic);
+      const float t1 = k == 0 ? __fmaf_rn(vh[2 * q + 1], sc, kRneMagic) : __fadd_rn(r1, kRneMagic);
       const float d0 = __fmaf_rn(t0, -256.0f, kRneMagic256), d1 = __fmaf_rn(t1, -256.0f, kRneMagic256);
       o[k][q] = pack_bf16_exact(d0, d1);
       if (k + 1 < kSlices) {
-        r0 = __fmaf_rn(r0, 256.0f, d0);
-        r1 = __fmaf_rn(r1, 256.0f, d1);
+        r0 = k == 0 ? __fmaf_rn(vh[2 * q], sc256, d0) : __fmaf_rn(r0, 256.0f, d0);
+        r1 = k == 0 ? __fmaf_rn(vh[2 * q + 1], sc256, d1) : __fmaf_rn(r1, 256.0f, d1);
         if (k == JOIN) {
           r0 = __fadd_rn(r0, l0);
           r1 = __fadd_rn(r1, l1);
