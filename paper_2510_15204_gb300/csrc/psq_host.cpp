@@ -149,7 +149,10 @@ struct Plan {
   struct Wave {
     int g0, g1, pb0, pb1, pn0, pn1, mb0, mb1, cb_off, n_ctas;
     int64_t jobs;
+    int64_t ph_off;  // its panel hint table in pack_hint
   };
+  std::vector<int> pack_hint;  // per wave, per kPackHintJobs packing jobs: the panel of the first
+  size_t o_ph = 0;
   std::vector<Wave> waves;
   size_t o_cb = 0;
   size_t o_mb = 0, o_mi = 0, o_pn = 0, o_pt = 0, nodes_off = 0, o_xi = 0, o_rc = 0, pack_off = 0;
@@ -843,6 +846,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       return (double)item_chunks(it) * (P.mblocks[it.block].b_panel < 0 ? 2.0 : 1.0);
     };
     P.cta_begin.clear();
+    P.pack_hint.clear();
     for (Plan::Wave& wv : P.waves) {
       // operand rows of the wave's grids from 0
       int64_t o = 0;
@@ -866,6 +870,11 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       }
       wv.pn1 = (int)pn_i;
       wv.jobs = jobs;
+      wv.ph_off = (int64_t)P.pack_hint.size();
+      for (int64_t jb = 0, k = wv.pn0; jb < jobs; jb += kPackHintJobs) {
+        while (k + 1 < wv.pn1 && P.panels[k + 1].job_begin <= jb) ++k;
+        P.pack_hint.push_back((int)(k - wv.pn0));
+      }
       pack_max = std::max(pack_max, pb);
       // its blocks: tiles (128 rows x 48 columns) x window ranges, work_split items per SM
       // (a static LPT deal then ends within a few percent of the mean), ranges of >= 4 windows
@@ -1083,6 +1092,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   P.o_mi = sec(sizeof(GemmItem) * P.mitems.size());
   P.o_cb = sec(sizeof(int) * P.cta_begin.size());
   P.o_pn = sec(sizeof(Panel) * P.panels.size());
+  P.o_ph = sec(sizeof(int) * P.pack_hint.size());
   P.o_pt = sec(sizeof(PairTile) * P.ptiles.size());
   P.o_status = sec(sizeof(int) * 4);
   P.o_xi = sec(sizeof(float2) * P.xi.size());
@@ -1142,6 +1152,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   put(P.o_mi, P.mitems.data(), sizeof(GemmItem) * P.mitems.size());
   put(P.o_cb, P.cta_begin.data(), sizeof(int) * P.cta_begin.size());
   put(P.o_pn, P.panels.data(), sizeof(Panel) * P.panels.size());
+  put(P.o_ph, P.pack_hint.data(), sizeof(int) * P.pack_hint.size());
   put(P.o_pt, P.ptiles.data(), sizeof(PairTile) * P.ptiles.size());
   put(P.o_xi, P.xi.data(), sizeof(float2) * P.xi.size());
   put(P.o_rc, P.rowc.data(), sizeof(double) * P.rowc.size());
@@ -1498,7 +1509,8 @@ psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_ou
       CUDA_TRY(mark(job, 1, s));
       CUDA_TRY(launch_eval_mixed(tw, nodes, (const float2*)(ws + P->o_xi), ops, ops_lo, s));
       CUDA_TRY(mark(job, 5, s));
-      CUDA_TRY(launch_pack(t.grids, panels + wv.pn0, wv.pn1 - wv.pn0, wv.jobs, t.pairs, ops, ops_lo, packed, s));
+      CUDA_TRY(launch_pack(t.grids, panels + wv.pn0, wv.pn1 - wv.pn0, (const int*)(ws + P->o_ph) + wv.ph_off, wv.jobs,
+                           t.pairs, ops, ops_lo, packed, s));
       CUDA_TRY(mark(job, 2, s));
       CUDA_TRY(launch_contract_ws(t.grids, (const MmaBlock*)(ws + P->o_mb), (const GemmItem*)(ws + P->o_mi),
                                   (const int*)(ws + P->o_cb) + wv.cb_off, wv.n_ctas, panels,

@@ -102,6 +102,7 @@ struct Panel {
   int64_t job_begin;  // first packing job (tile, window, 16-row group) of this panel, prefix over panels
 };
 constexpr int kZeroExp = -100000;
+constexpr int kPackHintJobs = 256;  // packing jobs per entry of a wave's panel hint table
 
 // The formed B operand of one tile of a 3-index block: column c (< kMmaN) is the product of
 // the staged basis rows dx[c] and dy[c] (indices into rows[], grid operand rows) and lands
@@ -189,8 +190,10 @@ cudaError_t launch_combine_rows(const float* h, const float* l, const double* rc
                                 double* out, cudaStream_t s);
 size_t ws_smem_bytes();
 cudaError_t prepare_kernels();  // per-device kernel attributes (context creation)
-cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
-                        const float* ops, const float* ops_lo, uint8_t* packed, cudaStream_t s);
+// hint: per block of kPackHintJobs jobs (numbered from 0 in panels[0]), the index of the panel
+// holding the block's first job (or NULL: bisection).
+cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, const int* hint, int64_t n_jobs,
+                        const short2* rows, const float* ops, const float* ops_lo, uint8_t* packed, cudaStream_t s);
 // Packed panels of the RI 4-index product from FP64 rows (panels[0] from srcA, panels[1] from
 // srcB, rows of n values); n_jobs covers both panels' packing jobs.
 cudaError_t launch_ri_pack(const Panel* panels, int64_t n_jobs, const double* srcA, const double* srcB, int n,

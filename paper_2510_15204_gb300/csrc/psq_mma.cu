@@ -450,11 +450,12 @@ __device__ __forceinline__ float pow2f(int k) {
 // Slicing.  A row's values in a 128-point window are scaled by 2^(7-e) (|v| < 2^e over the
 // window) and cut into five digits v ~ s0 + s1/256 + ... + s4/256^4 of integers (each the
 // nearest integer of what the previous digits left, times 256), exact in BF16: 39 bits of the
-// window's largest value.  For a double-float value the first three digits come from the hi
-// part (exactly); the lo part (|lo| <= 2^-24 |hi|) then joins the remainder, which rounds
-// once, at 2^-17 of the fourth digit's unit; s3 can reach 256.  Accumulation bound: the
-// order-k sum sum_{i+j=k} s_i t_j over 128 points stays below 128 x 114688 < 2^24 for every
-// k <= 4, so the FP32 tensor-core accumulators hold it exactly.
+// window's largest value.  Values are double-float pairs, products of two pairs left
+// unnormalised (|lo| <= 3 2^-24 |hi|); the first two digits come from the hi part (exactly),
+// then the lo part joins the remainder, which rounds once, at 2^-17 of the third digit's unit
+// (2^-40 of the window's largest value); s2 can reach 130.  Accumulation bound: the order-k
+// sum sum_{i+j=k} s_i t_j over 128 points stays below 128 x 114688 < 2^24 for every k <= 4,
+// so the FP32 tensor-core accumulators hold it exactly.
 
 namespace mma {
 
@@ -530,6 +531,15 @@ __device__ __forceinline__ uint32_t swz(int r, int j) { return (uint32_t)r * 64u
 
 }  // namespace mma
 
+// (xh + xl)(yh + yl) as hi = fl(xh yh) and the unnormalised lo = the exact error of that
+// product plus the cross terms (|lo| <= 3 2^-24 |hi|; the lo lo term, below 2^-48, dropped).
+__device__ __forceinline__ void prod_unnorm(float xh, float xl, float yh, float yl, float& h, float& l) {
+  h = __fmul_rn(xh, yh);
+  float e = __fmaf_rn(xh, yh, -h);
+  e = __fmaf_rn(xh, yl, e);
+  l = __fmaf_rn(xl, yh, e);
+}
+
 // Decodes packing job `job` (panel, tile, window, 16-row group) for this thread: 8 threads per
 // row, thread qq holding points [16 qq, 16 qq + 16) of the window (chunk 4 w + qq/2, 16-byte
 // groups 2 (qq % 2) and 2 (qq % 2) + 1 of its row).
@@ -537,11 +547,20 @@ struct PackPos {
   int pn, t, w, r, qq;
 };
 
-__device__ __forceinline__ PackPos pack_pos(int64_t job, const Panel* __restrict__ panels, int n_panels) {
-  int lo = 0, hi = n_panels;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (panels[mid].job_begin <= job) lo = mid; else hi = mid;
+// The panel of a job: from hint[job / kPackHintJobs] (the panel of that block's first job) by
+// a short forward scan, or by bisection when there is no hint.
+__device__ __forceinline__ PackPos pack_pos(int64_t job, const Panel* __restrict__ panels, int n_panels,
+                                            const int* __restrict__ hint) {
+  int lo = 0;
+  if (hint) {
+    lo = __ldg(hint + (job / kPackHintJobs));
+    while (lo + 1 < n_panels && panels[lo + 1].job_begin <= job) ++lo;
+  } else {
+    int hi = n_panels;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (panels[mid].job_begin <= job) lo = mid; else hi = mid;
+    }
   }
   const Panel& pn = panels[lo];
   const int G = pn.tr / kPackRows;
@@ -575,14 +594,14 @@ __device__ __forceinline__ void pack_store(const PackPos& P, const Panel& pn, co
   const int c = kChunksPerWin * P.w + (P.qq >> 1);
   if (c >= pn.nch || P.r >= rt) return;
   float sc, scj;
-  window_scales<2>(e, sc, scj);
+  window_scales<1>(e, sc, scj);
   uint8_t* dst = packed + pn.pack_off + (int64_t)P.t * pn.nch * (kSlices * pn.tr * kRowB) +
                  (int64_t)c * (kSlices * rt * kRowB);
   const int plane = rt * kRowB;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     uint4 wv[kSlices];
-    slice8_df<2>(h + 8 * j, l + 8 * j, sc, scj, wv);
+    slice8_df<1>(h + 8 * j, l + 8 * j, sc, scj, wv);
 #pragma unroll
     for (int k = 0; k < kSlices; ++k) *reinterpret_cast<uint4*>(dst + k * plane + swz(P.r, 2 * (P.qq & 1) + j)) = wv[k];
   }
@@ -591,10 +610,10 @@ __device__ __forceinline__ void pack_store(const PackPos& P, const Panel& pn, co
 // One CTA of 128 threads per packing job.  Values: source row times its weight row
 // (double-float products), zeros past K.
 __global__ void __launch_bounds__(128) pack_kernel(const DevGrid* __restrict__ grids, const Panel* __restrict__ panels,
-                                                   int n_panels, const short2* __restrict__ rows,
+                                                   int n_panels, const int* __restrict__ hint, const short2* __restrict__ rows,
                                                    const float* __restrict__ ops, const float* __restrict__ ops_lo,
                                                    uint8_t* __restrict__ packed) {
-  const PackPos P = pack_pos(blockIdx.x, panels, n_panels);
+  const PackPos P = pack_pos(blockIdx.x, panels, n_panels, hint);
   const Panel& pn = panels[P.pn];
   const DevGrid& g = grids[pn.grid];
   const int row = P.t * pn.tr + P.r;
@@ -632,9 +651,12 @@ __global__ void __launch_bounds__(128) pack_kernel(const DevGrid* __restrict__ g
     const float yh[4] = {bh.x, bh.y, bh.z, bh.w}, yl[4] = {bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const df v = mul >= 0 ? dfa::mul(df{xh[i], xl[i]}, df{yh[i], yl[i]}) : df{xh[i], xl[i]};
-      h[4 * i4 + i] = v.h;
-      l[4 * i4 + i] = v.l;
+      if (mul >= 0) {
+        prod_unnorm(xh[i], xl[i], yh[i], yl[i], h[4 * i4 + i], l[4 * i4 + i]);
+      } else {
+        h[4 * i4 + i] = xh[i];
+        l[4 * i4 + i] = xl[i];
+      }
     }
   }
   pack_store(P, pn, h, l, packed);
@@ -647,7 +669,7 @@ __global__ void __launch_bounds__(128) pack_kernel(const DevGrid* __restrict__ g
 // digits keep).
 __global__ void __launch_bounds__(128) ri_pack_kernel(const Panel* __restrict__ panels, const double* __restrict__ srcA,
                                                       const double* __restrict__ srcB, int n, uint8_t* __restrict__ packed) {
-  const PackPos P = pack_pos(blockIdx.x, panels, 2);
+  const PackPos P = pack_pos(blockIdx.x, panels, 2, nullptr);
   const Panel& pn = panels[P.pn];
   const double* src = P.pn ? srcB : srcA;
   const int row = P.t * pn.tr + P.r;
@@ -661,15 +683,6 @@ __global__ void __launch_bounds__(128) ri_pack_kernel(const Panel* __restrict__ 
     l[i] = (float)(v - (double)h[i]);
   }
   pack_store(P, pn, h, l, packed);
-}
-
-// (xh + xl)(yh + yl) as hi = fl(xh yh) and the unnormalised lo = the exact error of that
-// product plus the cross terms (|lo| <= 3 2^-24 |hi|; the lo lo term, below 2^-48, dropped).
-__device__ __forceinline__ void prod_unnorm(float xh, float xl, float yh, float yl, float& h, float& l) {
-  h = __fmul_rn(xh, yh);
-  float e = __fmaf_rn(xh, yh, -h);
-  e = __fmaf_rn(xh, yl, e);
-  l = __fmaf_rn(xl, yh, e);
 }
 
 // ------------------------------------------------------------------ warp-specialised contraction
@@ -1311,10 +1324,10 @@ cudaError_t prepare_kernels() {
   return cudaFuncSetAttribute(contract_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem_bytes());
 }
 
-cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, int64_t n_jobs, const short2* rows,
-                        const float* ops, const float* ops_lo, uint8_t* packed, cudaStream_t s) {
+cudaError_t launch_pack(const DevGrid* grids, const Panel* panels, int n_panels, const int* hint, int64_t n_jobs,
+                        const short2* rows, const float* ops, const float* ops_lo, uint8_t* packed, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
-  pack_kernel<<<(unsigned)n_jobs, 128, 0, s>>>(grids, panels, n_panels, rows, ops, ops_lo, packed);
+  pack_kernel<<<(unsigned)n_jobs, 128, 0, s>>>(grids, panels, n_panels, hint, rows, ops, ops_lo, packed);
   return cudaGetLastError();
 }
 
