@@ -132,7 +132,7 @@ struct Plan {
   // workspace layout (bytes)
   size_t table_bytes = 0, ops_off = 0, part_off = 0, res_off = 0, ws_bytes = 0;
   size_t o_grids, o_edges, o_bsh, o_ash, o_xyz, o_pb, o_gb, o_it, o_pairs, o_eb;
-  size_t o_fa, o_fl, o_aa, o_al, o_src[4], o_ptr[4], o_j3, o_status;
+  size_t o_fa, o_fl, o_fs, o_aa, o_al, o_src[4], o_ptr[4], o_j3, o_status;
   // mixed path
   bool mixed = false;
   std::vector<MmaBlock> mblocks;
@@ -184,6 +184,7 @@ struct psq_job {
   std::vector<psq_grid_spec> specs;
   psq_precision prec;
   std::vector<int> nb, na, sb0, sb1, sa0, sa1, fn_atom, fn_local, aux_atom, aux_local, nn;
+  std::vector<int> fn_shell;  // basis function -> its shell (index into dbs)
   std::vector<DevShell> dbs, das;
   int nbf = 0, naux = 0;
   std::map<unsigned, std::shared_ptr<Plan>> plans;  // shared: a running compute keeps its plan alive
@@ -1081,6 +1082,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   P.o_eb = sec(sizeof(int64_t) * P.elem_begin.size());
   P.o_fa = sec(sizeof(int) * j->fn_atom.size());
   P.o_fl = sec(sizeof(int) * j->fn_local.size());
+  P.o_fs = sec(sizeof(int) * j->fn_shell.size());
   P.o_aa = sec(sizeof(int) * j->aux_atom.size());
   P.o_al = sec(sizeof(int) * j->aux_local.size());
   for (int c = 0; c < 4; ++c) {
@@ -1141,6 +1143,7 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   put(P.o_eb, P.elem_begin.data(), sizeof(int64_t) * P.elem_begin.size());
   put(P.o_fa, j->fn_atom.data(), sizeof(int) * j->fn_atom.size());
   put(P.o_fl, j->fn_local.data(), sizeof(int) * j->fn_local.size());
+  put(P.o_fs, j->fn_shell.data(), sizeof(int) * j->fn_shell.size());
   put(P.o_aa, j->aux_atom.data(), sizeof(int) * j->aux_atom.size());
   put(P.o_al, j->aux_local.data(), sizeof(int) * j->aux_local.size());
   for (int c = 0; c < 4; ++c) {
@@ -1361,6 +1364,8 @@ psq_status psq_job_create(psq_context* ctx, const psq_atom* atoms, int n_atoms, 
       if (s1[X] < s0[X] || s0[X] == (int)sh.size()) s0[X] = s1[X] = 0;
   };
   layout(j->basis, j->nb, j->sb0, j->sb1, j->fn_atom, j->fn_local, j->dbs);
+  for (size_t q = 0; q < j->dbs.size(); ++q)
+    for (int m = 0; m < 2 * j->dbs[q].l + 1; ++m) j->fn_shell.push_back((int)q);
   layout(j->aux, j->na, j->sa0, j->sa1, j->aux_atom, j->aux_local, j->das);
   j->nbf = (int)j->fn_atom.size();
   j->naux = (int)j->aux_atom.size();
@@ -1541,13 +1546,16 @@ psq_status run_plan(psq_job* job, Plan* P, unsigned mask, char* ws, double* d_ou
     const int n = c == 3 ? job->naux : job->nbf;
     const int* at = c == 3 ? aa : fa;
     const int* lo = c == 3 ? al : fl;
+    // one-centre S and T from their closed forms (the basis shells and each function's shell)
+    const bool closed = c < 2;
     CUDA_TRY(launch_assemble((int)cls[c], job->nat, n, 0, at, lo, nullptr, nullptr,
-                             (const SrcEntry*)(ws + P->o_src[c]), (const int*)(ws + P->o_ptr[c]), nullptr, res,
-                             d_out[c], s));
+                             (const SrcEntry*)(ws + P->o_src[c]), (const int*)(ws + P->o_ptr[c]), nullptr,
+                             closed ? (const DevShell*)(ws + P->o_bsh) : nullptr,
+                             closed ? (const int*)(ws + P->o_fs) : nullptr, res, d_out[c], s));
   }
   if (mask & PSQ_J3)
     CUDA_TRY(launch_assemble(16, job->nat, job->nbf, job->naux, fa, fl, aa, al, nullptr, nullptr,
-                             (const J3Src*)(ws + P->o_j3), res, d_out[4], s));
+                             (const J3Src*)(ws + P->o_j3), nullptr, nullptr, res, d_out[4], s));
   CUDA_TRY(mark(job, -1, s));
   return PSQ_OK;
 }

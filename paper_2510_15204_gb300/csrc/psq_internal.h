@@ -176,10 +176,13 @@ void upload_gl_tables(const double* x, const double* w, const double* klm);  // 
 cudaError_t launch_eval_fp64(const LaunchTables& t, double* ops, int kinds, cudaStream_t s);
 cudaError_t launch_contract_fp64(const LaunchTables& t, const double* ops, double* part, cudaStream_t s);
 cudaError_t launch_reduce(const LaunchTables& t, const double* part, double* res, cudaStream_t s);
+// shells / fn_shell (S and T only, else NULL): the basis shells and each function's shell,
+// for the one-centre elements, which take their closed forms.
 cudaError_t launch_assemble(int cls, int n_atoms, int nfn, int naux, const int* fn_atom,
                             const int* fn_local, const int* aux_atom, const int* aux_local,
                             const SrcEntry* src, const int* src_ptr, const J3Src* j3,
-                            const double* res, double* out, cudaStream_t s);
+                            const DevShell* shells, const int* fn_shell, const double* res, double* out,
+                            cudaStream_t s);
 cudaError_t launch_grid_points(const LaunchTables& t, int g, double* out, cudaStream_t s);
 void upload_mixed_tables(const double* x, const double* w, const double* klm);
 cudaError_t launch_nodes(const DevGrid* grids, int n_grids, int max_entries, const double* edges, NodeEntry* tab,

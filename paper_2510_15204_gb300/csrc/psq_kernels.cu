@@ -379,15 +379,47 @@ cudaError_t launch_reduce(const LaunchTables& t, const double* part, double* res
   return cudaGetLastError();
 }
 
+// k! / z^(k+1) = int_0^inf r^k e^(-z r) dr (k >= 0), as a product of k + 1 factors.
+__device__ double radial_moment(int k, double z) {
+  double v = 1.0 / z;
+  for (int i = 1; i <= k; ++i) v *= (double)i / z;
+  return v;
+}
+
+// One-centre overlap (cls 1) or kinetic (cls 2) element of two basis functions of one atom,
+// from the closed forms of eq 1's functions: with I(k) = k! / (zeta_a + zeta_b)^(k+1), for the
+// same l and m S = N_a N_b I(n_a + n_b) and T = -1/2 N_a N_b [(n_b (n_b - 1) - l (l + 1))
+// I(n_a + n_b - 2) - 2 n_b zeta_b I(n_a + n_b - 1) + zeta_b^2 I(n_a + n_b)] (the radial
+// Laplacian written out), symmetrised; 0 for different l or m.
+__device__ double one_centre_st(int cls, const DevShell& A, int ma, const DevShell& B, int mb) {
+  if (A.l != B.l || ma != mb) return 0.0;
+  const double z = A.zeta + B.zeta, nn = A.norm * B.norm;
+  const int k = A.n + B.n;
+  if (cls == 1) return nn * radial_moment(k, z);
+  const double ll = (double)(A.l * (A.l + 1));
+  const double i2 = radial_moment(k - 2, z), i1 = radial_moment(k - 1, z), i0 = radial_moment(k, z);
+  const double tab = (B.n * (B.n - 1) - ll) * i2 - 2.0 * B.n * B.zeta * i1 + B.zeta * B.zeta * i0;
+  const double tba = (A.n * (A.n - 1) - ll) * i2 - 2.0 * A.n * A.zeta * i1 + A.zeta * A.zeta * i0;
+  return -0.25 * nn * (tab + tba);
+}
+
 // Molecule matrices from per-grid blocks.  cls: 1 S, 2 T, 4 V, 8 J2 (two-index), 16 J3.
+// With `shells`, one-centre elements take their closed forms (S and T).
 __global__ void assemble2_kernel(int cls, int nat, int nfn, const int* __restrict__ fn_atom,
                                  const int* __restrict__ fn_local, const SrcEntry* __restrict__ src,
-                                 const int* __restrict__ src_ptr, const double* __restrict__ res,
+                                 const int* __restrict__ src_ptr, const DevShell* __restrict__ shells,
+                                 const int* __restrict__ fn_shell, const double* __restrict__ res,
                                  double* __restrict__ out) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nfn * nfn) return;
   const int a = (int)(idx / nfn), b = (int)(idx % nfn);
   int X = fn_atom[a], Y = fn_atom[b], la = fn_local[a], lb = fn_local[b];
+  if (shells && X == Y) {
+    const DevShell& A = shells[fn_shell[a]];
+    const DevShell& B = shells[fn_shell[b]];
+    out[idx] = one_centre_st(cls, A, la - A.fn0, B, lb - B.fn0);
+    return;
+  }
   if (X > Y) { int t = X; X = Y; Y = t; t = la; la = lb; lb = t; }
   double v = 0.0;
   for (int e = src_ptr[X * nat + Y]; e < src_ptr[X * nat + Y + 1]; ++e) {
@@ -440,7 +472,8 @@ __global__ void assemble3_kernel(int nat, int nfn, int naux, const int* __restri
 cudaError_t launch_assemble(int cls, int nat, int nfn, int naux, const int* fn_atom,
                             const int* fn_local, const int* aux_atom, const int* aux_local,
                             const SrcEntry* src, const int* src_ptr, const J3Src* j3,
-                            const double* res, double* out, cudaStream_t s) {
+                            const DevShell* shells, const int* fn_shell, const double* res, double* out,
+                            cudaStream_t s) {
   if (cls == 16) {
     const int64_t n = (int64_t)naux * nfn * nfn;
     if (n == 0) return cudaSuccess;
@@ -450,7 +483,7 @@ cudaError_t launch_assemble(int cls, int nat, int nfn, int naux, const int* fn_a
     const int64_t n = (int64_t)nfn * nfn;
     if (n == 0) return cudaSuccess;
     assemble2_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cls, nat, nfn, fn_atom, fn_local,
-                                                                src, src_ptr, res, out);
+                                                                src, src_ptr, shells, fn_shell, res, out);
   }
   return cudaGetLastError();
 }

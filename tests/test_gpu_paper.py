@@ -122,11 +122,11 @@ def test_so2_tz_smallest_overlap_eigenvalue_on_the_gpu(P, ctx):
                                            ("QZ", {"S": 5.4e-12, "T": 3.0e-10, "V": 3.1e-7}),
                                            ("5Z", {"S": 8.9e-12, "T": 2.8e-10, "V": 3.2e-7})])
 def test_so2_table1_ps_rmse(P, ctx, basis, printed):
-    """Table 1's PS column: RMSE of the 26/32/14 grid against 80/70/50 for SO2.  V_ne (all
-    elements) within 3x of the printed value; overlap and kinetic two-centre blocks within 3x
-    of the printed all-element RMSE (this repository's one-centre elements, on the nearest
-    neighbour's pair grid, converge slower than the paper's; its text does not say how it
-    integrates them)."""
+    """Table 1's PS column: RMSE of the 26/32/14 grid against 80/70/50 for SO2, all elements.
+    One-centre S and T take their closed forms on both grids (the reading this repository
+    takes), under which the kinetic RMSE is the printed one within 15% for TZ, QZ and 5Z; the
+    overlap RMSE is below the printed one (7-14x here); V_ne (integrated on grids as before)
+    within 3x."""
     lo = run(P, ctx, synth.paper_job("SO2", spec=(26, 32, 14, 4, 4, 4, 3), mask=7, basis=basis), 7, P.FP64)
     hi = run(P, ctx, synth.paper_job("SO2", spec=(80, 70, 50, 4, 4, 4, 3), mask=7, basis=basis), 7, P.FP64)
     job = synth.paper_job("SO2", basis=basis)
@@ -137,10 +137,11 @@ def test_so2_table1_ps_rmse(P, ctx, basis, printed):
     assert printed["V"] / 3 < rv < 3 * printed["V"], rv
     for k in ("S", "T"):
         d = lo[k] - hi[k]
-        r2 = float(np.sqrt(np.mean(d[two] ** 2)))
-        # the reading in which one-centre elements come from their closed forms on both grids:
-        # their differences vanish and the all-element RMSE is the two-centre part alone
-        rc = float(np.sqrt(np.mean(np.where(two, d, 0.0) ** 2)))
-        print("SO2 %s PS RMSE %s: all elements %.2e, two-centre %.2e, one-centre exact %.2e (printed %.1e)"
-              % (basis, k, rmse(lo[k], hi[k]), r2, rc, printed[k]))
-        assert r2 < 3 * printed[k], (k, r2)
+        assert np.abs(d[~two]).max() < 1e-14, k  # one-centre: the same closed forms on both grids
+        r = rmse(lo[k], hi[k])
+        print("SO2 %s PS RMSE %s: all elements %.2e, two-centre %.2e (printed %.1e)"
+              % (basis, k, r, float(np.sqrt(np.mean(d[two] ** 2))), printed[k]))
+        if k == "T":
+            assert abs(r / printed[k] - 1.0) < 0.15, (k, r)
+        else:
+            assert r < printed[k], (k, r)
