@@ -94,6 +94,7 @@ def test_clf_convergence_with_grid_figs_3_4(P, ctx, cls):
     m = BIT[cls]
     ref = run(P, ctx, synth.clf_tz(spec=REF, mask=m), m, P.FP64)[cls]
     errs = [rmse(run(P, ctx, synth.clf_tz(spec=g + (4, 4, 4, 3), mask=m), m, P.FP64)[cls], ref) for g in S3]
+    print("\nClF %s RMSE over the Table S3 rows:" % cls, " ".join("%.1e" % e for e in errs))
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     bar = {"S": 3e-10, "J2": 2e-10, "J3": 3e-10, "T": 1e-6, "V": 3e-7}[cls]
     assert errs[-1] < bar, errs
