@@ -664,26 +664,64 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       if (g.C < 0) {
         const bool j3 = (mask & PSQ_J3) && g.nG > 0 && nl > 0;
         const bool j2 = (mask & PSQ_J2) && g.nG > 0;
-        int pu = -1, u_off = -1;
+        // the weighted potentials of the aux functions: one panel per atom (A tiles of one
+        // atom's rows, so that whole tiles of unused elements can be left out) when that takes
+        // no more 128-row tiles than one panel of both atoms' rows, else one panel
+        const int naA = j->na[g.A], naB = j->na[g.B];
+        auto ntiles = [](int r) { return (r + kMmaM - 1) / kMmaM; };
+        const bool split = naA > 0 && naB > 0 && ntiles(naA) + ntiles(naB) == ntiles(g.nG);
+        int pu[2] = {-1, -1}, u_off = -1;
         if (j3 || j2) {
           u_off = (int)P.pairs.size();
           for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_U + q, W));
-          pu = add_panel((int)gi, u_off, g.nG, kMmaM);
+          if (split) {
+            pu[0] = add_panel((int)gi, u_off, naA, kMmaM);
+            pu[1] = add_panel((int)gi, u_off + naA, naB, kMmaM);
+          } else {
+            pu[0] = add_panel((int)gi, u_off, g.nG, kMmaM);
+          }
         }
         if (j3) {
           // all local pairs i <= j, result columns in packed row-major order
           const int b_off = (int)P.pairs.size();
           for (int i = 0; i < nl; ++i)
             for (int jj = i; jj < nl; ++jj) P.pairs.push_back(make_short2(g.row_F + i, g.row_F + jj));
+          // pair tiles per class (A,A), (A,B), (B,B), in that order, each in 6 x 8 blocks of
+          // (i, j): 48 columns from at most 14 distinct rows
+          const int nA = g.nFA;
+          auto col_of = [&](int i, int jj) { return i * nl - i * (i - 1) / 2 + (jj - i); };
           std::vector<PairRef> pl;
-          // 6 x 8 blocks of (i, j): 48 columns from at most 14 distinct rows
-          for (int ib = 0; ib < nl; ib += 6)
-            for (int jb = ib / 8 * 8; jb < nl; jb += 8)
-              for (int i = ib; i < std::min(nl, ib + 6); ++i)
-                for (int jj = std::max(i, jb); jj < std::min(nl, jb + 8); ++jj)
-                  pl.push_back(PairRef{i * nl - i * (i - 1) / 2 + (jj - i), g.row_F + i, g.row_F + jj});
-          const auto tl = add_pair_tiles(pl);
-          gb.pair = add_mblock((int)gi, g.nG, nl * (nl + 1) / 2, u_off, b_off, pu, -1, tl.first, tl.second);
+          auto tiles = [&](int i0, int i1, int j0, int j1, bool upper) {
+            pl.clear();
+            for (int ib = i0; ib < i1; ib += 6)
+              for (int jb = upper ? j0 + (ib - i0) / 8 * 8 : j0; jb < j1; jb += 8)
+                for (int i = ib; i < std::min(i1, ib + 6); ++i)
+                  for (int jj = upper ? std::max(i, jb) : jb; jj < std::min(j1, jb + 8); ++jj)
+                    pl.push_back(PairRef{col_of(i, jj), g.row_F + i, g.row_F + jj});
+            return add_pair_tiles(pl);
+          };
+          // (without the split: one class of all pairs, fewer partial tiles)
+          const auto tAA = split ? tiles(0, nA, 0, nA, true) : tiles(0, nl, 0, nl, true);
+          const auto tAB = split ? tiles(0, nA, nA, nl, false) : std::make_pair(tAA.first + tAA.second, 0);
+          const auto tBB = split ? tiles(nA, nl, nA, nl, true) : std::make_pair(tAB.first, 0);
+          // an atom's rows need the one-centre pairs (its own functions) only where this grid
+          // is its one-centre grid; the other classes are two-centre terms of this pair
+          auto here = [&](int Y, int Wt, int X) {
+            const GridKey k = grid_for(j, Y, Wt, X);
+            return k.A == g.A && k.B == g.B && k.C < 0;
+          };
+          const int end_all = tBB.first + tBB.second;
+          if (split) {
+            // rows of A: (A,A) if here, then (A,B), (B,B); rows of B: (A,A), (A,B), then (B,B)
+            // if here; the two blocks' results are consecutive (rows of A, then rows of B)
+            const int t0 = here(g.A, g.A, g.A) ? tAA.first : tAB.first;
+            gb.pair = add_mblock((int)gi, naA, nl * (nl + 1) / 2, u_off, b_off, pu[0], -1, t0, end_all - t0);
+            const int t1 = here(g.B, g.B, g.B) ? end_all : tAB.first + tAB.second;
+            add_mblock((int)gi, naB, nl * (nl + 1) / 2, u_off + naA, b_off, pu[1], -1, tAA.first, t1 - tAA.first);
+          } else {
+            gb.pair = add_mblock((int)gi, g.nG, nl * (nl + 1) / 2, u_off, b_off, pu[0], -1, tAA.first,
+                                 end_all - tAA.first);
+          }
         }
         if ((mask & (PSQ_S | PSQ_T | PSQ_V)) && nl > 0) {
           // 2-index block: [w lap chi | w chi | w/r_A chi | w/r_B chi] against chi
@@ -713,7 +751,12 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
           const int b_off = (int)P.pairs.size();
           for (int q = 0; q < g.nG; ++q) P.pairs.push_back(make_short2(g.row_G + q, -1));
           const int pg = add_panel((int)gi, b_off, g.nG, kMmaN);
-          gb.j2 = add_mblock((int)gi, g.nG, g.nG, u_off, b_off, pu, pg, -1, 0);
+          if (split) {  // rows of A, then rows of B (consecutive results, as one nG x nG block)
+            gb.j2 = add_mblock((int)gi, naA, g.nG, u_off, b_off, pu[0], pg, -1, 0);
+            add_mblock((int)gi, naB, g.nG, u_off + naA, b_off, pu[1], pg, -1, 0);
+          } else {
+            gb.j2 = add_mblock((int)gi, g.nG, g.nG, u_off, b_off, pu[0], pg, -1, 0);
+          }
         }
       } else if (g.nFA > 0 && g.nFB > 0) {
         const bool j3 = (mask & PSQ_J3) && g.nG > 0;
