@@ -349,7 +349,8 @@ def time_ri(J2, J3, stream, reps=20):
 
 def recorded_traffic(kernel, workload, precision):
     """DRAM bytes of `kernel` per bench step from profiles/traffic.txt, if recorded for the current
-    kernel source (null once the source changed since the counters were taken)."""
+    sources of the kernel and its planner (null once either changed since the counters were
+    taken)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -357,9 +358,13 @@ def recorded_traffic(kernel, workload, precision):
         f = line.split("#")[0].split()
         if len(f) != 6 or f[0] != kernel or f[1] != workload or f[2] != precision:
             continue
-        src = os.path.join(ROOT, "paper_2510_15204_gb300", "csrc", f[3])
-        if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == f[4]:
-            return int(f[5])
+        # the kernel's source files (joined by "+": the kernel and the planner that shapes
+        # its launches), hashed together
+        srcs = [os.path.join(ROOT, "paper_2510_15204_gb300", "csrc", n) for n in f[3].split("+")]
+        if all(os.path.exists(x) for x in srcs):
+            h = hashlib.sha256(b"".join(open(x, "rb").read() for x in srcs)).hexdigest()[:16]
+            if h == f[4]:
+                return int(f[5])
     return None
 
 
