@@ -147,15 +147,17 @@ def test_issued_flops_bound_the_useful_work(P, ctx, make):
     """The tensor-pipe roofline counts issued MMAs: fifteen slice products (orders 0..4 of
     five 8-bit slices) per useful product, plus tile padding and the duplicated triangle of
     symmetric blocks, so never less than 30 FLOPs per useful contraction; on the large blocks
-    of C3H6 padding stays under 2.2x (its 3-index A tiles hold 72 or 90 aux rows of 128).  The FP64 path issues at least the useful 2 FLOPs per
-    contraction."""
+    of C3H6 padding stays under 1.9x (its 3-index A tiles hold 72 or 90 aux rows of 128, and
+    the one-centre pair tiles that a base grid's rows of one atom do not use are left out:
+    55.7 FLOPs per contraction, 60.6 with them).  The FP64 path issues at least the useful 2
+    FLOPs per contraction."""
     job = make(0)
     for prec, lo in ((P.MIXED, 30.0), (P.FP64, 2.0)):
         J = P.Job.from_synth(ctx, job, prec)
         st = J.stats(job.mask)
         assert st["issued_flops"] >= lo * st["contractions"]
         if make is synth.c3h6:
-            assert st["issued_flops"] <= 2.2 * lo * st["contractions"]
+            assert st["issued_flops"] <= 1.9 * lo * st["contractions"]
 
 
 def test_noalloc_and_wait_limit_refuse_without_a_device(P, ctx):
