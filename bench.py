@@ -64,6 +64,8 @@ def parse():
                          "(n x m) matrices")
     ap.add_argument("--rates", default="10,20,50,100,200,500", help="serving: Poisson arrival rates (jobs/s)")
     ap.add_argument("--jobs", type=int, default=300, help="serving: jobs per rate")
+    ap.add_argument("--serve-window", type=int, default=32,
+                    help="serving: jobs submitted and unfinished at most (the rest queue on the host)")
     ap.add_argument("--baseline-jobs", type=int, default=6, help="serving: jobs timed on the per-job FP64 path")
     return ap.parse_args()
 
@@ -433,8 +435,8 @@ def serve_main(args):
     """Poisson stream of random molecules (2..9 atoms, Z in {1,6,7,8}, DZ/TZ/QZ-sized bases,
     config-2 grids) through the continuous-batching server (mixed precision, within 1e-9 of
     the FP64 oracle), swept over arrival rates, against the same stream's first jobs run one by
-    one on the plain FP64 path.  Latency is from a job's arrival to its results in host memory;
-    p99 over the rate's jobs (--jobs, 300 by default)."""
+    one on the plain FP64 path.  Latency is from a job's arrival to its results in host memory
+    (host queueing included); p99 over the rate's jobs (--jobs, 300 by default)."""
     import threading
     import numpy as np
     import torch
@@ -452,26 +454,71 @@ def serve_main(args):
     for rate in [float(x) for x in args.rates.split(",")]:
         stream = synth.serving_stream(seed=args.seed, rate=rate, n_jobs=args.jobs)
         jobs = [P.Job.from_synth(ctx, j, P.MIXED) for _, j in stream]
-        outs = [{k: torch.empty(sh, dtype=torch.float64).pin_memory() for k, sh in J.out_shapes(mask).items()}
-                for J in jobs]
         for J in jobs:
             J.workspace_bytes(mask)  # plan up front: planning is host work, not serving latency
         work = sum(J.stats(mask)["contractions"] for J in jobs)
-        tickets = [None] * len(jobs)
+        n = len(jobs)
+        tickets, outs, sub_t = [None] * n, [None] * n, [0.0] * n
+        lat = [0.0] * n
+        state = {"done": 0}
+        cv = threading.Condition()
+        window = args.serve_window
         t0 = time.perf_counter()
 
         def feeder():
-            for i, (t_arr, _) in enumerate(stream):
-                d = t0 + t_arr - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                tickets[i] = server.submit(jobs[i], mask, outs[i])
+            # jobs arrive at their stream times; at most `window` are submitted and unfinished
+            # (the rest wait on the host, inside their measured latency); each job's pinned
+            # result buffers exist from its submission to its completion
+            try:
+                for i, (t_arr, _) in enumerate(stream):
+                    with cv:
+                        while i - state["done"] >= window and "error" not in state:
+                            cv.wait()
+                    if "error" in state:
+                        return
+                    out = {k: torch.empty(sh, dtype=torch.float64).pin_memory()
+                           for k, sh in jobs[i].out_shapes(mask).items()}
+                    d = t0 + t_arr - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    outs[i] = out
+                    sub_t[i] = time.perf_counter()
+                    t = server.submit(jobs[i], mask, out)
+                    with cv:
+                        tickets[i] = t
+                        cv.notify_all()
+            except Exception as e:  # let the collector stop too
+                with cv:
+                    state["error"] = repr(e)
+                    cv.notify_all()
 
-        th = threading.Thread(target=feeder)
-        th.start()
-        th.join()
-        lat = [server.wait(t) for t in tickets]
-        wall = time.perf_counter() - t0
+        def collector():
+            try:
+                for i in range(n):
+                    with cv:
+                        while tickets[i] is None and "error" not in state:
+                            cv.wait()
+                    if "error" in state:
+                        return
+                    served = server.wait(tickets[i])  # submission -> results in host memory
+                    lat[i] = (sub_t[i] - (t0 + stream[i][0])) + served
+                    outs[i] = None
+                    with cv:
+                        state["done"] += 1
+                        cv.notify_all()
+            except Exception as e:
+                with cv:
+                    state["error"] = repr(e)
+                    cv.notify_all()
+
+        threads = [threading.Thread(target=feeder), threading.Thread(target=collector)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        if "error" in state:
+            raise RuntimeError("serving run failed: " + state["error"])
+        wall = max(stream[i][0] + lat[i] for i in range(n))  # arrival of the first job at 0
         res["rates"].append({"rate_per_s": rate, "jobs": len(jobs), "p50_s": float(np.percentile(lat, 50)),
                              "p99_s": float(np.percentile(lat, 99)), "throughput_jobs_per_s": len(jobs) / wall,
                              "contractions_per_s": work / wall, "precision": "mixed (1e-9 absolute)"})

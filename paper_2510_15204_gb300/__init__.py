@@ -421,8 +421,12 @@ class Server:
         return bool(d.value), lat.value
 
     def wait(self, ticket, timeout_s=600.0):
+        """Latency of a finished ticket (s, submission to results in host memory); the server no
+        longer needs the job or its host buffers afterwards."""
         _check(lib().psq_server_wait(self.handle, ticket, timeout_s))
-        return self.poll(ticket)[1]
+        lat = self.poll(ticket)[1]
+        self._keep.pop(ticket, None)
+        return lat
 
     def close(self):
         if getattr(self, "handle", None):
