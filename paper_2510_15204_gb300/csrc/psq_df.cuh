@@ -195,14 +195,17 @@ PSQ_DF_FN void real_ylm(int lmax, df ux, df uy, df uz, df* Y, const float* rcp) 
   df C[7], S[7];
   C[0] = mk(1.0f);
   S[0] = mk(0.0f);
+#pragma unroll 1
   for (int m = 1; m <= lmax; ++m) {
     C[m] = sub(mul(ux, C[m - 1]), mul(uy, S[m - 1]));
     S[m] = add(mul(ux, S[m - 1]), mul(uy, C[m - 1]));
   }
   float dfact = 1.0f;  // (2m-1)!!, exact in FP32 for m <= 6
+#pragma unroll 1
   for (int m = 0; m <= lmax; ++m) {
     if (m > 0) dfact *= (float)(2 * m - 1);
     df q2 = mk(0.0f), q1 = mk(dfact);
+#pragma unroll 1
     for (int l = m; l <= lmax; ++l) {
       df q;
       if (l == m) {
@@ -247,12 +250,14 @@ PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fa
     if (x.h < (float)k1) {
       df t = div_k(mk(1.0f), k1, rcp), s = t;
       int j = 1;
+#pragma unroll 1  // data-dependent trip counts: rolled loops keep the code small
       for (; j < 100; ++j) {  // double-float terms while they reach 2^-24 of the sum
         t = div_k(mul(t, x), k1 + j, rcp);
         s = add_same(s, t);
         if (t.h < 5.9604645e-8f * s.h) break;
       }
       float tf = t.h, sf = 0.0f;  // the rest in FP32 (each term below 2^-24 of the sum)
+#pragma unroll 1
       for (++j; j < 400 && k1 + j < 128; ++j) {
         tf *= x.h * rcp[k1 + j];
         sf += tf;
@@ -262,6 +267,7 @@ PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fa
       inner = mul(mul(pow_i(x, n + 1), ex), s);
     } else {
       df t = mk(1.0f), s = mk(1.0f);
+#pragma unroll 1
       for (int j = 1; j < k1; ++j) {
         t = div_k(mul(t, x), j, rcp);
         s = add_same(s, t);
@@ -270,6 +276,7 @@ PSQ_DF_FN df radial(int kind, int n, int l, df x, df ex, df ix, const float2* fa
       inner = mul_pow(mul(df{fact[k1 - 1].x, fact[k1 - 1].y}, q), ix, l + 1);
     }
     df t = mk(1.0f), s = mk(1.0f);
+#pragma unroll 1
     for (int j = 1; j < k2; ++j) {
       t = div_k(mul(t, x), j, rcp);
       s = add_same(s, t);

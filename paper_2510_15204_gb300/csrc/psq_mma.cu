@@ -154,6 +154,7 @@ __device__ __forceinline__ void eval_shells_df(const DevShell* __restrict__ sh, 
                                                int s0, int s1, df rho, const df* Y, float* __restrict__ oh,
                                                float* __restrict__ ol, int64_t ld, int64_t p, int row_a,
                                                int kind_a, int row_b, int kind_b, const float2* etab) {
+#pragma unroll 1  // one shell at a time: unrolled copies only grow the code
   for (int s = s0; s < s1; ++s) {
     const DevShell q = sh[s];
     const df x = dfa::mul(ld2(xi[s - s0]), rho);
@@ -162,6 +163,7 @@ __device__ __forceinline__ void eval_shells_df(const DevShell* __restrict__ sh, 
     const int base = q.l * q.l + q.l;
     if (row_a >= 0) {
       const df ra = dfa::radial(kind_a, q.n, q.l, x, ex, ix, c_factd, c_rcpf);
+#pragma unroll 1
       for (int m = -q.l; m <= q.l; ++m) {
         const df v = dfa::mul(ra, Y[base + m]);
         const int64_t o = (int64_t)(row_a + q.fn0 + q.l + m) * ld + p;
@@ -171,6 +173,7 @@ __device__ __forceinline__ void eval_shells_df(const DevShell* __restrict__ sh, 
     }
     if (row_b >= 0) {
       const df rb = dfa::radial(kind_b, q.n, q.l, x, ex, ix, c_factd, c_rcpf);
+#pragma unroll 1
       for (int m = -q.l; m <= q.l; ++m) {
         const df v = dfa::mul(rb, Y[base + m]);
         const int64_t o = (int64_t)(row_b + q.fn0 + q.l + m) * ld + p;
