@@ -12,7 +12,9 @@
  * (Section 4): every matrix element is integrated on exactly one grid, picked by the
  * distinct centres of its integrand (one centre: the pair grid of that atom and its nearest
  * neighbour, ties to the lower index; two: their pair grid; three: the pair grid of the two
- * basis-function atoms refined around the third).
+ * basis-function atoms refined around the third).  One-centre overlap and kinetic elements
+ * are not integrated: they take their closed forms (the reading under which Table 1's
+ * kinetic RMSE is reproduced).
  *
  * Conventions.  Atomic units (bohr).  Shells must be listed grouped by atom in ascending
  * atom order.  Function order: atom, then shell as listed, then m = -l..l of real
