@@ -12,6 +12,8 @@ __constant__ double c_glx[kMaxQ + 1][kMaxQ];  // Gauss-Legendre nodes on [-1,1],
 __constant__ double c_glw[kMaxQ + 1][kMaxQ];  // and weights
 __constant__ double c_klm[(kMaxL + 1) * (kMaxL + 1)];  // harmonic norms, sqrt2 for m != 0
 __constant__ double c_fact[2 * kMaxN + 4];             // k!
+constexpr int kRcpD = 128;
+__constant__ double c_rcpd[kRcpD];                     // 1/k (c_rcpd[0] unused)
 
 void upload_gl_tables(const double* x, const double* w, const double* klm) {
   cudaMemcpyToSymbol(c_glx, x, sizeof(double) * (kMaxQ + 1) * kMaxQ);
@@ -21,7 +23,16 @@ void upload_gl_tables(const double* x, const double* w, const double* klm) {
   f[0] = 1.0;
   for (int k = 1; k < 2 * kMaxN + 4; ++k) f[k] = f[k - 1] * k;
   cudaMemcpyToSymbol(c_fact, f, sizeof(f));
+  double r[kRcpD];
+  r[0] = 0.0;
+  for (int k = 1; k < kRcpD; ++k) r[k] = 1.0 / k;
+  cudaMemcpyToSymbol(c_rcpd, r, sizeof(r));
 }
+
+// x / k for a positive integer k: a multiply by the rounded reciprocal from a table (one
+// rounding more than a division, a relative 2^-52 per term; FP64 division is a long
+// instruction sequence on this GPU's FP64 pipe), a division past the table.
+__device__ __forceinline__ double div_int(double x, int k) { return k < kRcpD ? x * c_rcpd[k] : x / k; }
 
 struct Pt {
   double P[3], dA[3], dB[3];
@@ -153,21 +164,24 @@ __device__ double aux_pot_radial(int n, int l, double zeta, double norm, double 
   const double ex = exp(-x);
   double inner;
   if (x < (double)k1) {
-    double term = 1.0 / k1, sum = term;
+    double term = c_rcpd[k1], sum = term;
+#pragma unroll 1
     for (int i = 1; i < 1000; ++i) {
-      term *= x / (k1 + i);
+      term *= div_int(x, k1 + i);
       sum += term;
       if (term <= 1e-17 * sum) break;
     }
     inner = ipow(r, n + 1) * ex * sum;  // x^k1 / (z^k1 r^(l+1)) = r^(n+1)
   } else {
     double t = 1.0, s = 1.0;
-    for (int j = 1; j < k1; ++j) { t *= x / j; s += t; }
+#pragma unroll 1
+    for (int j = 1; j < k1; ++j) { t *= div_int(x, j); s += t; }
     const double f = c_fact[k1 - 1];
     inner = (f - f * ex * s) / (ipow(zeta, k1) * ipow(r, l + 1));
   }
   double t = 1.0, s = 1.0;
-  for (int j = 1; j < k2; ++j) { t *= x / j; s += t; }
+#pragma unroll 1
+  for (int j = 1; j < k2; ++j) { t *= div_int(x, j); s += t; }
   const double outer = c_fact[k2 - 1] * ex * s * ipow(r, l) / ipow(zeta, k2);
   return 4.0 * M_PI / (2 * l + 1) * norm * (inner + outer);
 }
