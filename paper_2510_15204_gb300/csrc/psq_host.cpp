@@ -557,6 +557,19 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
         for (int x = 0; x < tm; ++x)
           for (int y = 0; y < tn; ++y) P.items.push_back(GemmItem{(int)bi, x, y, c});
     }
+    // Largest items first (outputs x points, a formed pair column costing one more product per
+    // point): the CTA scheduler hands out blocks in index order, so the last wave holds the
+    // small items and the tail of the launch is short.
+    auto fp_cost = [&](const GemmItem& it) {
+      const GemmBlock& b = P.gblocks[it.block];
+      const int64_t K = P.grids[b.grid].K;
+      const int64_t csz = (K + b.n_chunks - 1) / b.n_chunks;
+      const int64_t pts = std::max<int64_t>(0, std::min<int64_t>(K, (int64_t)it.chunk * csz + csz) - (int64_t)it.chunk * csz);
+      const int rows = std::min(b.tile_m, b.m - it.tm * b.tile_m), cols = std::min(b.tile_n, b.n - it.tn * b.tile_n);
+      return (double)pts * ((double)rows * cols + rows + (b.b_mode == 1 ? 2.0 : 1.0) * cols);
+    };
+    std::stable_sort(P.items.begin(), P.items.end(),
+                     [&](const GemmItem& x, const GemmItem& y) { return fp_cost(x) > fp_cost(y); });
     P.elem_begin.resize(P.gblocks.size() + 1);
     P.elem_begin[0] = 0;
     for (size_t bi = 0; bi < P.gblocks.size(); ++bi)
