@@ -463,8 +463,19 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
   auto J3at = [&](int X, int Y, int W) -> J3Src& { return P.j3[((size_t)X * nat + Y) * nat + W]; };
   if (!P.mixed) {
     // FP64 path: one block per (grid, class) and per (grid, aux atom, basis atom pair)
-    std::vector<int64_t> s_loc(P.grids.size(), -1), t_loc(P.grids.size(), -1), va_loc(P.grids.size(), -1),
-        vb_loc(P.grids.size(), -1), vc_loc(P.grids.size(), -1), j2_loc(P.grids.size(), -1);
+    // On a pair grid (A < B) only the blocks that some element reads: S the A x B block (the
+    // one-centre S and T come from their closed forms); T the A x B block and its mirror
+    // (B rows against A's kinetic columns), averaged; (P|Q) the A x B block and its mirror, and
+    // the A x A (B x B) block where the grid is A's (B's) one-centre grid; V_ne of nucleus A the
+    // A x B block, the B x B block (B's functions in A's field) and the A x A block where the
+    // grid is A's one-centre grid (and likewise for nucleus B).
+    struct Fp2 { int64_t ab = -1, ba = -1, aa = -1, bb = -1; };
+    std::vector<int64_t> s_loc(P.grids.size(), -1), vc_loc(P.grids.size(), -1);
+    std::vector<Fp2> t_loc(P.grids.size()), j2_loc(P.grids.size()), va_loc(P.grids.size()), vb_loc(P.grids.size());
+    auto own_grid = [&](const DevGrid& g, int X) {
+      const GridKey k = grid_for(j, X, X, X);
+      return k.A == g.A && k.B == g.B && k.C == -1;
+    };
     auto add_block = [&](int g, int a_row, int m, int b_row, int n, int b_mode, int pair_off, int d_row) {
       GemmBlock b{};
       b.grid = g; b.a_row = a_row; b.m = m; b.b_row = b_row; b.n = n; b.b_mode = b_mode;
@@ -479,15 +490,33 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
       const int w = g.row_W;
       const int gint = (int)gi;
       if (g.C < 0) {
-        if (nl > 0) {
-          if (mask & PSQ_S) s_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w);
-          if (mask & PSQ_T) t_loc[gi] = add_block(gint, g.row_F, nl, g.row_L, nl, 0, 0, w);
-          if (mask & PSQ_V) {
-            va_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 1);
-            vb_loc[gi] = add_block(gint, g.row_F, nl, g.row_F, nl, 0, 0, w + 2);
+        if (g.nFA > 0 && g.nFB > 0) {
+          if (mask & PSQ_S) s_loc[gi] = add_block(gint, g.row_F, g.nFA, g.row_F + g.nFA, g.nFB, 0, 0, w);
+          if (mask & PSQ_T) {
+            t_loc[gi].ab = add_block(gint, g.row_F, g.nFA, g.row_L + g.nFA, g.nFB, 0, 0, w);
+            t_loc[gi].ba = add_block(gint, g.row_F + g.nFA, g.nFB, g.row_L, g.nFA, 0, 0, w);
           }
         }
-        if ((mask & PSQ_J2) && g.nG > 0) j2_loc[gi] = add_block(gint, g.row_U, g.nG, g.row_G, g.nG, 0, 0, w);
+        if (mask & PSQ_V) {
+          const bool oA = own_grid(g, g.A), oB = own_grid(g, g.B);
+          for (int c = 0; c < 2; ++c) {  // nucleus A (weight row w + 1), nucleus B (w + 2)
+            Fp2& v = c == 0 ? va_loc[gi] : vb_loc[gi];
+            if (g.nFA > 0 && g.nFB > 0) v.ab = add_block(gint, g.row_F, g.nFA, g.row_F + g.nFA, g.nFB, 0, 0, w + 1 + c);
+            if (g.nFA > 0 && (c == 1 || oA)) v.aa = add_block(gint, g.row_F, g.nFA, g.row_F, g.nFA, 0, 0, w + 1 + c);
+            if (g.nFB > 0 && (c == 0 || oB))
+              v.bb = add_block(gint, g.row_F + g.nFA, g.nFB, g.row_F + g.nFA, g.nFB, 0, 0, w + 1 + c);
+          }
+        }
+        if (mask & PSQ_J2) {
+          const int naA = j->na[g.A], naB = j->na[g.B];
+          if (naA > 0 && naB > 0) {
+            j2_loc[gi].ab = add_block(gint, g.row_U, naA, g.row_G + naA, naB, 0, 0, w);
+            j2_loc[gi].ba = add_block(gint, g.row_U + naA, naB, g.row_G, naA, 0, 0, w);
+          }
+          if (naA > 0 && own_grid(g, g.A)) j2_loc[gi].aa = add_block(gint, g.row_U, naA, g.row_G, naA, 0, 0, w);
+          if (naB > 0 && own_grid(g, g.B))
+            j2_loc[gi].bb = add_block(gint, g.row_U + naA, naB, g.row_G + naA, naB, 0, 0, w);
+        }
         if (mask & PSQ_J3) {
           const int atoms2[2] = {g.A, g.B};
           for (int xi = 0; xi < 2; ++xi) {
@@ -581,9 +610,12 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
         if (X > Y || mask == 0) continue;
         const int gb = gidx[grid_for(j, X, Y, X)];
         const DevGrid& G = P.grids[gb];
-        const int nl = G.nFA + G.nFB, oX = local_off(G, X), oY = local_off(G, Y);
-        if (mask & PSQ_S) P.src[0].push_back(SrcEntry{s_loc[gb], nl, oX, oY, oY, oX, 0, 0, 0, 1.0});
-        if (mask & PSQ_T) P.src[1].push_back(SrcEntry{t_loc[gb], nl, oX, oY, oY, oX, 0, 0, 0, 1.0});
+        // X < Y: the grid of (X, Y) is the pair grid with A = X, B = Y; X == Y: closed forms
+        // for S and T (no source), (P|Q) from the one-centre grid's own block
+        if (X < Y && (mask & PSQ_S) && s_loc[gb] >= 0)
+          P.src[0].push_back(SrcEntry{s_loc[gb], G.nFB, 0, 0, 0, 0, 0, 0, 0, 1.0, 0, 0});
+        if (X < Y && (mask & PSQ_T) && t_loc[gb].ab >= 0)
+          P.src[1].push_back(SrcEntry{t_loc[gb].ab, G.nFB, 0, 0, 0, 0, 0, 0, 0, 1.0, t_loc[gb].ba, G.nFA});
         if (mask & PSQ_V) {
           for (int C = 0; C < nat; ++C) {
             const GridKey k = grid_for(j, X, Y, C);
@@ -593,15 +625,20 @@ psq_status make_plan(psq_job* j, unsigned mask, Plan& P) {
             if (k.C >= 0) {
               P.src[2].push_back(SrcEntry{vc_loc[gv], H.nFB, 0, 0, 0, 0, 0, 0, 0, z});
             } else {
-              const int64_t off = C == H.A ? va_loc[gv] : vb_loc[gv];
-              const int hX = local_off(H, X), hY = local_off(H, Y);
-              P.src[2].push_back(SrcEntry{off, H.nFA + H.nFB, hX, hY, hY, hX, 0, 0, 0, z});
+              // C is A or B of the pair grid; X < Y: (X, Y) = (A, B), the A x B block; X == Y:
+              // the X x X block
+              const Fp2& v = C == H.A ? va_loc[gv] : vb_loc[gv];
+              const int64_t off = X < Y ? v.ab : (X == H.A ? v.aa : v.bb);
+              P.src[2].push_back(SrcEntry{off, j->nb[Y], 0, 0, 0, 0, 0, 0, 0, z, 0, 0});
             }
           }
         }
         if (mask & PSQ_J2) {
-          const int aX = aux_off(G, X), aY = aux_off(G, Y);
-          P.src[3].push_back(SrcEntry{j2_loc[gb], G.nG, aX, aY, aY, aX, 0, 0, 0, 1.0});
+          const Fp2& b = j2_loc[gb];
+          if (X < Y && b.ab >= 0)
+            P.src[3].push_back(SrcEntry{b.ab, j->na[Y], 0, 0, 0, 0, 0, 0, 0, 1.0, b.ba, j->na[X]});
+          const int64_t own = X == G.A ? b.aa : b.bb;
+          if (X == Y && own >= 0) P.src[3].push_back(SrcEntry{own, j->na[X], 0, 0, 0, 0, 0, 0, 0, 1.0, 0, 0});
         }
       }
     }

@@ -136,14 +136,17 @@ struct GemmItem { int block, tm, tn, chunk; };
 
 // Assembly sources (Section 4: each element from exactly one grid, V_ne summed over nuclei).
 // Two-index element (a on X, b on Y, local indices la, lb) from block M = res + off:
-//   mode 0: M[(rX+la)*ld + cY+lb], averaged with its mirror M[(rY+lb)*ld + cX+la] where the
-//           class is symmetrised;
+//   mode 0: M[(rX+la)*ld + cY+lb], averaged with its mirror M2[(rY+lb)*ld2 + cX+la] where the
+//           class is symmetrised (M2 = res + off2 with leading dimension ld2 when ld2 > 0,
+//           else M and ld: the mirror in the same block);
 //   mode 1: M[p*ld + cX*cs], p = packed index of the local pair (rX+la, cY+lb) over nloc;
 //   mode 2: M[p*ld + cX*cs], p = la*nloc + lb (a rectangular pair list).
 struct SrcEntry {
   int64_t off;
   int ld, rX, cY, rY, cX, mode, nloc, cs;
   double z;
+  int64_t off2;
+  int ld2;
 };
 // Three-index element (P on X, i on Y, j on W; Y <= W): res[off + p*s_pair + lP*s_aux] with
 // p the packed (mode 1) index of (offY+li, offW+lj) over nloc or (mode 0) (offY+li)*nloc +

@@ -441,10 +441,13 @@ __global__ void assemble2_kernel(int cls, int nat, int nfn, const int* __restric
     const double* M = res + s.off;
     if (s.mode == 0) {
       const double m1 = M[(int64_t)(s.rX + la) * s.ld + s.cY + lb];
-      const double m2 = M[(int64_t)(s.rY + lb) * s.ld + s.cX + la];
-      if (cls == 2) v += -0.25 * (m1 + m2);
-      else if (cls == 8 || X == Y) v += s.z * 0.5 * (m1 + m2);
-      else v += s.z * m1;
+      if (cls == 2 || cls == 8 || X == Y) {
+        const double* M2 = s.ld2 > 0 ? res + s.off2 : M;
+        const double m2 = M2[(int64_t)(s.rY + lb) * (s.ld2 > 0 ? s.ld2 : s.ld) + s.cX + la];
+        v += (cls == 2 ? -0.25 : s.z * 0.5) * (m1 + m2);
+      } else {
+        v += s.z * m1;
+      }
     } else {
       int64_t p;
       if (s.mode == 1) {
