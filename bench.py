@@ -767,7 +767,11 @@ def main():
     roof["kernel"] = kind
     roof["launches_per_step"] = kcount / args.steps
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("achieved") else None
-    roof["traffic"] = recorded_traffic(kind, args.workload, args.precision)
+    # DRAM bytes per launch (the step's recorded bytes over its launches, as `achieved` is the
+    # step's work over its launches' time), and per step
+    step_bytes = recorded_traffic(kind, args.workload, args.precision)
+    roof["traffic"] = step_bytes / roof["launches_per_step"] if step_bytes and roof["launches_per_step"] else None
+    roof["traffic_per_step"] = step_bytes
     roof["share"] = kms / sum(v[0] for v in prof.values())
 
     line = {

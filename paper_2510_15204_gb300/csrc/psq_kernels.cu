@@ -158,10 +158,9 @@ __device__ __forceinline__ double ipow(double x, int n) {
 // Radial factor of V^P (eq 16 written out by the Laplace expansion of 1/r12):
 // 4 pi/(2l+1) N [ gamma(n+l+2, zr)/(z^(n+l+2) r^(l+1)) + Gamma(n-l+1, zr) r^l / z^(n-l+1) ].
 // gamma by its positive series below x = k (no cancellation), by (k-1)! - Gamma above.
-__device__ double aux_pot_radial(int n, int l, double zeta, double norm, double r) {
-  const double x = zeta * r;
+__device__ double aux_pot_radial(int n, int l, double zeta, double norm, double r, double ex) {
+  const double x = zeta * r;  // ex = e^-x
   const int k1 = n + l + 2, k2 = n - l + 1;
-  const double ex = exp(-x);
   double inner;
   if (x < (double)k1) {
     double term = c_rcpd[k1], sum = term;
@@ -186,27 +185,34 @@ __device__ double aux_pot_radial(int n, int l, double zeta, double norm, double 
   return 4.0 * M_PI / (2 * l + 1) * norm * (inner + outer);
 }
 
-// Evaluates the shells [s0, s1) of one centre at distance r, offset d, writing chi (or V^P)
-// rows from row0 of the operand matrix.  kind: 0 chi, 1 lap chi (kinetic operand), 2 V^P.
-__device__ __forceinline__ void eval_shells(const DevShell* __restrict__ sh, int s0, int s1,
-                                            double r, const double* Y, double* __restrict__ out,
-                                            int64_t ld, int64_t p, int row0, int kind) {
+// Evaluates the shells [s0, s1) of one centre at distance r (ir = 1/r) for one or two row
+// kinds (kind: 0 chi, 1 lap chi (kinetic operand), 2 V^P), writing from rows row_a and row_b
+// (-1: not wanted) of the operand matrix; e^-zeta r is computed once per shell for both.
+__device__ __forceinline__ void eval_shells(const DevShell* __restrict__ sh, int s0, int s1, double r, double ir,
+                                            const double* Y, double* __restrict__ out, int64_t ld, int64_t p,
+                                            int row_a, int kind_a, int row_b, int kind_b) {
   for (int s = s0; s < s1; ++s) {
     const DevShell q = sh[s];
-    double radial;
-    if (kind == 2) {
-      radial = aux_pot_radial(q.n, q.l, q.zeta, q.norm, r);
-    } else {
-      radial = q.norm * ipow(r, q.n - 1) * exp(-q.zeta * r);
-      if (kind == 1) {
-        const double f = (q.n * (q.n - 1) - q.l * (q.l + 1)) / (r * r) - 2.0 * q.n * q.zeta / r +
-                         q.zeta * q.zeta;
-        radial *= f;
-      }
-    }
+    const double ex = exp(-q.zeta * r);
     const int base = q.l * q.l + q.l;
-    for (int m = -q.l; m <= q.l; ++m)
-      out[(int64_t)(row0 + q.fn0 + q.l + m) * ld + p] = radial * Y[base + m];
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      const int row0 = h == 0 ? row_a : row_b, kind = h == 0 ? kind_a : kind_b;
+      if (row0 < 0) continue;
+      double radial;
+      if (kind == 2) {
+        radial = aux_pot_radial(q.n, q.l, q.zeta, q.norm, r, ex);
+      } else {
+        radial = q.norm * ipow(r, q.n - 1) * ex;
+        if (kind == 1) {
+          const double f = (q.n * (q.n - 1) - q.l * (q.l + 1)) * (ir * ir) - 2.0 * q.n * q.zeta * ir +
+                           q.zeta * q.zeta;
+          radial *= f;
+        }
+      }
+      for (int m = -q.l; m <= q.l; ++m)
+        out[(int64_t)(row0 + q.fn0 + q.l + m) * ld + p] = radial * Y[base + m];
+    }
   }
 }
 
@@ -245,12 +251,12 @@ __global__ void __launch_bounds__(128) eval_fp64_kernel(LaunchTables t, double* 
     for (int c = 0; c < 2; ++c) {
       const int s0 = c == 0 ? g.shb_A0 : g.shb_B0, s1 = c == 0 ? g.shb_A1 : g.shb_B1;
       if (s1 <= s0) continue;
-      const double r = c == 0 ? pt.rA : pt.rB;
+      const double r = c == 0 ? pt.rA : pt.rB, ir = 1.0 / r;
       const double* d = c == 0 ? pt.dA : pt.dB;
-      real_ylm(shells_lmax(t.bshell, s0, s1), d[0] / r, d[1] / r, d[2] / r, Y);
+      real_ylm(shells_lmax(t.bshell, s0, s1), d[0] * ir, d[1] * ir, d[2] * ir, Y);
       const int roff = c == 0 ? 0 : g.nFA;
-      if (g.row_F >= 0) eval_shells(t.bshell, s0, s1, r, Y, base, ld, p, g.row_F + roff, 0);
-      if (g.row_L >= 0) eval_shells(t.bshell, s0, s1, r, Y, base, ld, p, g.row_L + roff, 1);
+      eval_shells(t.bshell, s0, s1, r, ir, Y, base, ld, p, g.row_F >= 0 ? g.row_F + roff : -1, 0,
+                  g.row_L >= 0 ? g.row_L + roff : -1, 1);
     }
   }
   // aux functions and their potentials
@@ -265,9 +271,10 @@ __global__ void __launch_bounds__(128) eval_fp64_kernel(LaunchTables t, double* 
       if (atom == g.A) { d = pt.dA; r = pt.rA; }
       else if (atom == g.B) { d = pt.dB; r = pt.rB; }
       else { d = dC; r = rC; }
-      real_ylm(shells_lmax(t.ashell, s0, s1), d[0] / r, d[1] / r, d[2] / r, Y);
-      if (g.row_G >= 0) eval_shells(t.ashell, s0, s1, r, Y, base, ld, p, g.row_G + roff, 0);
-      if (g.row_U >= 0) eval_shells(t.ashell, s0, s1, r, Y, base, ld, p, g.row_U + roff, 2);
+      const double ir = 1.0 / r;
+      real_ylm(shells_lmax(t.ashell, s0, s1), d[0] * ir, d[1] * ir, d[2] * ir, Y);
+      eval_shells(t.ashell, s0, s1, r, ir, Y, base, ld, p, g.row_G >= 0 ? g.row_G + roff : -1, 0,
+                  g.row_U >= 0 ? g.row_U + roff : -1, 2);
       int nf = 0;
       for (int s = s0; s < s1; ++s) nf += 2 * t.ashell[s].l + 1;
       roff += nf;
