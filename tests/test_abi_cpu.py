@@ -150,14 +150,18 @@ def test_issued_flops_bound_the_useful_work(P, ctx, make):
     of C3H6 padding stays under 1.9x (its 3-index A tiles hold 72 or 90 aux rows of 128, and
     the one-centre pair tiles that a base grid's rows of one atom do not use are left out:
     55.7 FLOPs per contraction, 60.6 with them).  The FP64 path issues at least the useful 2
-    FLOPs per contraction."""
+    FLOPs per contraction and at most 15% more on the triatomic and C3H6 (a pair grid's blocks
+    hold only what an element reads; the symmetrised T and (P|Q) elements add their mirror
+    blocks: 1.11x and 1.02x)."""
     job = make(0)
     for prec, lo in ((P.MIXED, 30.0), (P.FP64, 2.0)):
         J = P.Job.from_synth(ctx, job, prec)
         st = J.stats(job.mask)
         assert st["issued_flops"] >= lo * st["contractions"]
-        if make is synth.c3h6:
+        if make is synth.c3h6 and prec == P.MIXED:
             assert st["issued_flops"] <= 1.9 * lo * st["contractions"]
+        if make is not synth.h2_fp64 and prec == P.FP64:
+            assert st["issued_flops"] <= 1.15 * lo * st["contractions"]
 
 
 def test_noalloc_and_wait_limit_refuse_without_a_device(P, ctx):
