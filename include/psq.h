@@ -270,12 +270,13 @@ psq_status psq_ri_solve(int n, int64_t m, const double* d_L, double* d_B, void* 
 psq_status psq_ri_eri(int n, int64_t m, const double* d_B, int64_t c0, int64_t nc, int64_t d0, int64_t nd,
                       double* d_out, void* stream);
 
-/* The same block on the tensor cores (the mixed path's arithmetic, no paper counterpart): the
- * pair columns of B are cut into four 8-bit slices under a power-of-two scale per pair and
- * 128 aux functions, the slice products of orders 0..3 accumulate exactly in FP32 and the
- * aux ranges add in FP64.  Error: within about 2e-9 of sum_w n_w M_w(ij) M_w(kl) over the
- * windows w of 128 aux functions (n_w of them), M_w(p) the largest |B[R][p]| in w: each value
- * keeps 31 bits relative to its window's largest.  d_workspace (256-byte aligned)
+/* The same block on the tensor cores (the mixed path's arithmetic, no paper counterpart): each
+ * FP64 value of B's pair columns is split into a double-float pair and cut into five 8-bit
+ * digits under a power-of-two scale per pair and 128 aux functions, the slice products of
+ * orders 0..4 accumulate exactly in FP32 and the aux ranges add in FP64.  Error: each value
+ * keeps 39 bits relative to its window's largest, so the block is within about 2^-38 of
+ * sum_w n_w M_w(ij) M_w(kl) over the windows w of 128 aux functions (n_w of them), M_w(p) the
+ * largest |B[R][p]| in w (the tests assert the looser 2e-9).  d_workspace (256-byte aligned)
  * needs psq_ri_eri_mixed_workspace(n, nc, nd) bytes on the current device; its first int is
  * the contraction's status word (nonzero: a bounded wait expired, d_out undefined).  Errors
  * as psq_ri_eri, and PSQ_ERR_OOM for a smaller workspace, PSQ_ERR_UNSUPPORTED for blocks of

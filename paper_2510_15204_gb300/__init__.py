@@ -158,7 +158,8 @@ def ri_eri(B, c0, nc, d0, nd, out=None, stream=None):
 
 
 def ri_eri_mixed(B, c0, nc, d0, nd, out=None, ws=None, stream=None):
-    """ri_eri on the tensor cores (8-bit slice products, ~2e-9 of the window-maximum bound);
+    """ri_eri on the tensor cores (five 8-bit digits per value, within ~2^-38 of the
+    window-maximum bound);
     ws: a uint8 CUDA tensor of at least ri_eri_mixed_workspace bytes (allocated if None).
     Asynchronous."""
     import torch

@@ -158,8 +158,8 @@ def test_triatomic_eri_parity(P):
 
 def window_bound(Ba, Bb):
     """sum over 128-row aux windows of (rows in the window) x (window max |a|) x (window max |b|)
-    per element: the scale the slices resolve to 2^-31 (each value keeps 31 bits relative to
-    its window's largest)."""
+    per element: the scale the digits resolve to about 2^-38 (each value keeps 39 bits relative
+    to its window's largest: five 8-bit digits of its double-float split)."""
     out = 0.0
     for w0 in range(0, Ba.shape[0], 128):
         ma = np.abs(Ba[w0:w0 + 128]).max(axis=0)
@@ -171,8 +171,9 @@ def window_bound(Ba, Bb):
 @pytest.mark.parametrize("n,m,blk", [(1, 9, (0, 9, 0, 9)), (37, 150, (17, 70, 90, 60)), (82, 676, (0, 676, 0, 676)),
                                      (200, 3000, (100, 1300, 500, 700))])
 def test_eri_mixed_within_stated_error(P, n, m, blk):
-    """Tensor-core (ij|kl) against the FP64 product: within 2e-9 (about 4 x 2^-31) of the
-    window bound; ragged aux counts, pair ranges and blocks, aux rows of scales e^-3..e^3."""
+    """Tensor-core (ij|kl) against the FP64 product: within 2e-9 of the window bound (a loose
+    bound, kept from a four-digit version; five digits give about 2^-38); ragged aux counts,
+    pair ranges and blocks, aux rows of scales e^-3..e^3."""
     import torch
     rng = np.random.default_rng(n + m)
     B = rng.standard_normal((n, m)) * np.exp(rng.uniform(-3, 3, (n, 1)))
