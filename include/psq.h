@@ -285,6 +285,16 @@ psq_status psq_ri_eri_mixed_workspace(int n, int64_t nc, int64_t nd, size_t* byt
 psq_status psq_ri_eri_mixed(int n, int64_t m, const double* d_B, int64_t c0, int64_t nc, int64_t d0, int64_t nd,
                             double* d_out, void* d_workspace, size_t ws_bytes, void* stream);
 
+/* Peak rates of the current device's arithmetic pipes, measured (no paper counterpart; the
+ * denominators of the FP64- and FP32-bound rooflines): independent dependent-FMA chains in
+ * FP64 and in FP32 and a chain of the special-function unit's ex2.approx, each launched as 4
+ * CTAs x 256 threads per SM, 8 chains per thread, ~30 ms: the fastest of three launches timed
+ * by CUDA events on `stream` after a warm-up launch.  Outputs (host doubles; any may be
+ * NULL): FP64 and FP32 TFLOP/s (2 FLOPs per FMA), SFU operations in G/s.  Uses no device
+ * memory of the caller; synchronises the stream.  Errors: PSQ_ERR_CUDA when there is no
+ * device or a launch or event call fails. */
+psq_status psq_measure_peaks(void* stream, double* fp64_tflops, double* fp32_tflops, double* sfu_gops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ SIGNATURES = [
     ("psq_ri_eri_mixed_workspace", _I, [_I, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_SZ)]),
     ("psq_ri_eri_mixed", _I, [_I, ctypes.c_int64, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                               _VP, _VP, _SZ, _VP]),
+    ("psq_measure_peaks", _I, [_VP, _PD, _PD, _PD]),
 ]
 
 
@@ -120,6 +121,14 @@ def _dev_f64(t, name):
     if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
         raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
     return ctypes.c_void_p(t.data_ptr())
+
+
+def measure_peaks(stream=None):
+    """Measured FP64 / FP32 FMA rates (TFLOP/s) and SFU rate (G ops/s) of the current device
+    (psq_measure_peaks); synchronises the stream."""
+    f64, f32, sfu = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().psq_measure_peaks(_stream_ptr(stream), ctypes.byref(f64), ctypes.byref(f32), ctypes.byref(sfu)))
+    return {"fp64_tflops": f64.value, "fp32_tflops": f32.value, "sfu_gops": sfu.value}
 
 
 def ri_factor(J2, L=None, stream=None):

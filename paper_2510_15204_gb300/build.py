@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpsq.so")
-SOURCES = ["psq_host.cpp", "psq_server.cpp", "psq_kernels.cu", "psq_mma.cu", "psq_static.cu", "psq_ri.cu"]
+SOURCES = ["psq_host.cpp", "psq_server.cpp", "psq_kernels.cu", "psq_mma.cu", "psq_static.cu", "psq_ri.cu",
+           "psq_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
