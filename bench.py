@@ -275,7 +275,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------------------ traffic record
+# ------------------------------------------------------------------------------ RI timing
 
 def time_ri(J2, J3, stream, reps=20):
     """Device time of the RI 4-index assembly (eq 14) on the job's own (P|Q) and (P|ij): Cholesky
@@ -348,6 +348,8 @@ def time_ri(J2, J3, stream, reps=20):
             "eri_block": {"fp64_ms": t64, "fp64_tflops": eflops / (t64 / 1e3) / 1e12, "tensor_ms": tmx,
                           "tensor_useful_tflops": eflops / (tmx / 1e3) / 1e12, "tensor_max_dev_rel": dev}}
 
+
+# ------------------------------------------------------------------------------ traffic record
 
 def recorded_traffic(kernel, workload, precision):
     """DRAM bytes of `kernel` per bench step from profiles/traffic.txt, if recorded for the current
