@@ -210,3 +210,13 @@ def test_ri_entry_points_validate_arguments_without_a_gpu(P):
     assert L.psq_ri_eri_mixed(3, 10, dummy, 8, 5, 0, 2, dummy, dummy, 1 << 20, None) == 1  # c0 + nc > m
     assert L.psq_ri_eri_mixed(3, 10, dummy, 0, 2, 0, 2, dummy, ctypes.c_void_p(64 + 8), 1 << 20, None) == 1  # ws align
     assert L.psq_ri_eri_mixed(3, 10, dummy, 0, 0, 0, 2, None, None, 0, None) == 0  # empty block
+
+
+def test_measure_peaks_refuses_without_a_device(P):
+    """The pipe-rate probe returns PSQ_ERR_CUDA with a message where no CUDA device exists."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    L = P.lib()
+    assert L.psq_measure_peaks(None, None, None, None) == 3
+    assert b"no CUDA device" in L.psq_last_error()
