@@ -29,10 +29,10 @@ Parity is pinned, not assumed: ``tests/test_oracle_*.py`` check this module agai
 closed-form 1s-1s integrals, textbook Gauss-Legendre rules, scipy's Legendre functions and
 incomplete gamma, Poisson's equation for V^P, partition invariants of the grid, symmetry,
 permutation equivariance, and the SO2 overlap eigenvalue printed in Section 4.  The
-3-centre V_ne and (P|ij) values have no closed form; for 1s, 2s and 2p functions they are
-pinned by convergence, as the refined grid grows, to an independent evaluation by Gaussian
-transforms (``tests/gauss_transform.py``), besides the grid-choice and convergence
-invariants.
+3-centre V_ne and (P|ij) values have no closed form; for basis functions up to 4f and a 1s
+aux function they are pinned by convergence, as the refined grid grows, to an independent
+evaluation by Gaussian transforms (``tests/gauss_transform.py``), besides the grid-choice
+and convergence invariants.
 """
 from __future__ import annotations
 

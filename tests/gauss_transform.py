@@ -181,3 +181,128 @@ def three_index_coulomb(alpha, C, za, A, zb, B, h=0.125):
     i_e = product_integral(za, A, zb, B, C, "exp", alpha=alpha, h=h)
     return (norm1s(za) * norm1s(zb) * norm1s(alpha) * 8.0 * math.pi / alpha ** 3
             * (i_c - i_s - 0.5 * alpha * i_e))
+
+
+# ------------------------------------------------------------------ any n, l
+
+def solid_harmonic(l, m, rng_seed=11):
+    """Coefficients {(i, j, k): c} of the homogeneous polynomial r^l Y_lm(x, y, z) = sum c x^i
+    y^j z^k for the real orthonormal harmonics without the Condon-Shortley phase (m > 0: cos,
+    m < 0: sin), fitted by least squares to scipy's complex harmonics at random points (exact
+    up to rounding: the monomials of degree l span the solid harmonics)."""
+    import scipy.special as sp
+    mons = [(i, j, l - i - j) for i in range(l + 1) for j in range(l + 1 - i)]
+    rng = np.random.default_rng(rng_seed)
+    d = rng.normal(size=(4 * len(mons) + 20, 3))
+    r = np.linalg.norm(d, axis=1)
+    theta, phi = np.arccos(d[:, 2] / r), np.arctan2(d[:, 1], d[:, 0])
+    am = abs(m)
+    c = sp.sph_harm_y(l, am, theta, phi) if hasattr(sp, "sph_harm_y") else sp.sph_harm(am, l, phi, theta)
+    y = c.real if m == 0 else math.sqrt(2.0) * (-1) ** am * (c.real if m > 0 else c.imag)
+    X = np.stack([d[:, 0] ** i * d[:, 1] ** j * d[:, 2] ** k for (i, j, k) in mons], axis=1)
+    coef = np.linalg.lstsq(X, y * r ** l, rcond=None)[0]
+    return {mo: float(v) for mo, v in zip(mons, coef) if abs(v) > 1e-12}
+
+
+def _radial_weights(zeta, k, h, lo=-14.0, hi=18.0):
+    """Weights of r^k e^{-zeta r} = (-d/dzeta)^k e^{-zeta r} on the nodes u = e^x: (-1)^k times
+    the k-th zeta-derivative of zeta/(2 sqrt(pi)) u^{-3/2} e^{-zeta^2/(4u)}, with
+    d^k/dzeta^k e^{-zeta^2/(4u)} = (-1)^k (4u)^{-k/2} H_k(zeta/(2 sqrt u)) e^{-zeta^2/(4u)}
+    (physicists' Hermite polynomials) and d^k (zeta E) = zeta E^(k) + k E^(k-1)."""
+    from numpy.polynomial import hermite
+    x = np.arange(lo, hi + 0.5 * h, h)
+    u = np.exp(x)
+    y = zeta / (2.0 * np.sqrt(u))
+    E = np.exp(-y * y)
+
+    def dE(q):
+        if q < 0:
+            return np.zeros_like(u)
+        return (-1) ** q * (4.0 * u) ** (-q / 2.0) * hermite.hermval(y, [0] * q + [1]) * E
+
+    dk = zeta * dE(k) + k * dE(k - 1)
+    return u, h * u * (-1) ** k / (2.0 * math.sqrt(math.pi)) * u ** -1.5 * dk
+
+
+def sto_nlm(n, l, m, zeta):
+    """Normalised STO of eq 1 (N = (2 zeta)^(n+1/2)/sqrt((2n)!)) as (zeta, radial power
+    n - 1 - l, {monomial: coefficient}) of N r^(n-1-l) e^{-zeta r} (r^l Y_lm)."""
+    N = (2.0 * zeta) ** (n + 0.5) / math.sqrt(math.factorial(2 * n))
+    return (zeta, n - 1 - l, {mo: N * c for mo, c in solid_harmonic(l, m).items()})
+
+
+def _moments(p, PA, PB, la, lb):
+    """m[i][j] = int (t - A)^i (t - B)^j e^{-p (t - P)^2} dt / sqrt(pi/p) along one axis, with
+    PA = P - A, PB = P - B, by the recurrences m[i+1][j] = PA m[i][j] + (i m[i-1][j] +
+    j m[i][j-1]) / (2p) and m[i][j+1] = PB m[i][j] + (i m[i-1][j] + j m[i][j-1]) / (2p)
+    (differentiate the Gaussian about P), m[0][0] = 1."""
+    h2 = 0.5 / p
+    m = [[None] * (lb + 1) for _ in range(la + 1)]
+    m[0][0] = np.ones_like(p)
+    for i in range(la + 1):
+        for j in range(lb + 1):
+            if i == 0 and j == 0:
+                continue
+            if i > 0:
+                v = PA * m[i - 1][j]
+                if i > 1:
+                    v = v + (i - 1) * h2 * m[i - 2][j]
+                if j > 0:
+                    v = v + j * h2 * m[i - 1][j - 1]
+            else:
+                v = PB * m[i][j - 1]
+                if j > 1:
+                    v = v + (j - 1) * h2 * m[i][j - 2]
+            m[i][j] = v
+    return m
+
+
+def nlm_matrix(fas, A, fbs, B, C, op, alpha=0.0, h=0.125, chunk=48):
+    """M[i][j] = int a_i(r) b_j(r) O(r_C) d^3r for STOs from sto_nlm() (any n, l) on A and B and
+    O as in sto_matrix(): the polynomial factors integrate as products of one-dimensional
+    moments of the product Gaussian about its centre P = (aA + bB + cC)/p.  The operator's
+    nodes are processed `chunk` at a time."""
+    A, B, C = (np.asarray(v, dtype=float) for v in (A, B, C))
+    WA = np.stack([_radial_weights(f[0], f[1], h)[1] for f in fas])
+    WB = np.stack([_radial_weights(f[0], f[1], h)[1] for f in fbs])
+    u = _radial_weights(1.0, 0, h)[0]
+    if op == "coulomb":
+        uc, wc = _coulomb_factor(0.0, 0.5 * h)
+    elif op == "screened":
+        uc, wc = _coulomb_factor(alpha, 0.5 * h)
+    elif op == "exp":
+        uc, wc = _sto_factor(alpha, h)
+    elif op == "one":
+        uc, wc = np.zeros(1), np.ones(1)
+    else:
+        raise ValueError(op)
+    mons_a = sorted({mo for f in fas for mo in f[2]})
+    mons_b = sorted({mo for f in fbs for mo in f[2]})
+    CA = np.array([[f[2].get(mo, 0.0) for mo in mons_a] for f in fas])
+    CB = np.array([[f[2].get(mo, 0.0) for mo in mons_b] for f in fbs])
+    la = max(sum(mo) for mo in mons_a)
+    lb = max(sum(mo) for mo in mons_b)
+    AB2, AC2, BC2 = float(np.sum((A - B) ** 2)), float(np.sum((A - C) ** 2)), float(np.sum((B - C) ** 2))
+    a, b = u[None, :, None], u[None, None, :]
+    out = np.zeros((len(fas), len(fbs)))
+    for c0 in range(0, len(uc), chunk):
+        c = uc[c0:c0 + chunk, None, None]
+        w = wc[c0:c0 + chunk, None, None]
+        p = a + b + c
+        g = w * (math.pi / p) ** 1.5 * np.exp(-(a * b * AB2 + a * c * AC2 + b * c * BC2) / p)
+        mom = [_moments(p, (b * (B[k] - A[k]) + c * (C[k] - A[k])) / p,
+                        (a * (A[k] - B[k]) + c * (C[k] - B[k])) / p, la, lb) for k in range(3)]
+        for ia, (i1, j1, k1) in enumerate(mons_a):
+            for ib, (i2, j2, k2) in enumerate(mons_b):
+                T = np.sum(g * mom[0][i1][i2] * mom[1][j1][j2] * mom[2][k1][k2], axis=0)
+                out += np.outer(CA[:, ia], CB[:, ib]) * (WA @ T @ WB.T)
+    return out
+
+
+def nlm_three_index_matrix(alpha, C, fas, A, fbs, B, h=0.125):
+    """(P|a_i b_j) for a normalised 1s aux function P of exponent alpha on C and STOs from
+    sto_nlm() on A and B."""
+    i_c = nlm_matrix(fas, A, fbs, B, C, "coulomb", h=h)
+    i_s = nlm_matrix(fas, A, fbs, B, C, "screened", alpha=alpha, h=h)
+    i_e = nlm_matrix(fas, A, fbs, B, C, "exp", alpha=alpha, h=h)
+    return norm1s(alpha) * 8.0 * math.pi / alpha ** 3 * (i_c - i_s - 0.5 * alpha * i_e)
