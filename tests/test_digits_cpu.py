@@ -7,7 +7,10 @@ relies on (the tensor-core contraction of eq 9 on 8-bit digits):
   rounding leaves 2^-33 of the scaled unit and the lo word's join rounds once more at most as
   much, against a largest scaled value of at least 64 (the digits span 39 bits);
 * the order-k sums sum_{i+j=k} s_i t_j over a 128-point window stay below 2^24 in digit units,
-  so FP32 accumulation of the slice products is exact.
+  so FP32 accumulation of the slice products is exact;
+* the fold (order 1 split at 2^24, one TwoSum into the double-float sum, orders 2-4 as one
+  FP32 term) accumulates windows to within 2^-38 of sum_w 128 max|a_w| max|b_w| of the exact
+  dot product of the double-float inputs.
 
 Each kernel step is an FP32 add or FMA whose exact result fits in an FP64 significand (a power
 -of-two scale times an FP32 value plus a multiple of the spacing), so computing it in FP64 and
@@ -110,3 +113,62 @@ def test_order_sums_are_exact_in_fp32():
             top = max(top, tot)
     bound = 128 * 114688  # the design's bound: 128 points x 7 x 128^2
     assert top < bound < 2 ** 24, (top, bound)
+
+
+def _two_sum(a, b):
+    s = np.float32(a + b)
+    bb = np.float32(s - a)
+    return s, np.float32(np.float32(a - np.float32(s - bb)) + np.float32(b - bb))
+
+
+def _fast_two_sum(a, b):
+    s = np.float32(a + b)
+    return s, np.float32(b - np.float32(s - a))
+
+
+def _fma(a, b, c):
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _fold(o, sc, H, L):
+    """One window's five order sums into the running double-float sum (H, L), step by step as
+    the fold warps do it."""
+    mag = np.float32(1.5 * 2.0 ** 47)
+    q1 = np.float32(np.float32(o[1] + mag) - mag)  # nearest multiple of 2^24
+    r1 = np.float32(o[1] - q1)
+    s0h, s0l = _two_sum(H, np.float32(_fma(q1, np.float32(2.0 ** -8), o[0]) * sc))
+    tail = np.float32(_fma(r1, np.float32(2.0 ** -8), _fma(o[2], np.float32(2.0 ** -16), _fma(
+        o[4], np.float32(2.0 ** -32), np.float32(o[3] * np.float32(2.0 ** -24))))) * sc)
+    lo = np.float32(L + np.float32(s0l + tail))
+    return _fast_two_sum(s0h, lo)
+
+
+def test_window_fold_matches_the_exact_dot_product():
+    """Digits of one A row and one B column per window, their exact order sums (as the tensor
+    cores accumulate them), the fold with the window scales 2^(e_a - 15) 2^(e_b - 15): against
+    the exact sum of the double-float products over 1-19 windows (measured worst 2^-41.3 of
+    the window bound)."""
+    import math
+    rng = np.random.default_rng(8)
+    worst = 0.0
+    for _ in range(120):
+        span = float(rng.choice([0.0, 3.0, 10.0]))
+        H = L = np.float32(0.0)
+        exact = bound = 0.0
+        for _w in range(int(rng.integers(1, 20))):
+            ah, al, a = unnormalised_products(rng, 128, span)
+            bh, bl, b = unnormalised_products(rng, 128, span)
+            ea, eb = window_exponent(ah), window_exponent(bh)
+            da = split(ah, al, ea).astype(np.float64)
+            db = split(bh, bl, eb).astype(np.float64)
+            o = []
+            for k in range(5):
+                ok = sum(float(np.dot(da[i], db[k - i])) for i in range(k + 1))
+                assert float(np.float32(ok)) == ok  # exact in FP32
+                o.append(np.float32(ok))
+            H, L = _fold(o, np.float32(2.0 ** (ea - 15) * 2.0 ** (eb - 15)), H, L)
+            exact += math.fsum(a * b)
+            bound += 128 * np.abs(a).max() * np.abs(b).max()
+        err = abs(float(H) + float(L) - exact) / bound
+        worst = max(worst, err)
+    assert worst <= 2.0 ** -38, worst
